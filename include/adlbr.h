@@ -1,0 +1,163 @@
+/*
+ * adlbr.h -- C ABI of the GB300 (sm_103a) AD-LBR library, libadlbr.so.
+ *
+ * AD-LBR is the anisotropic-diffusion scheme of J. Fehrenbach and J.-M.
+ * Mirebeau, "Sparse Non-Negative Stencils for Anisotropic Diffusion"
+ * (arXiv 1301.3925).  For a field of symmetric positive definite tensors D(z)
+ * on a Cartesian grid, the library builds at every point the stencil V(z)
+ * (6 offsets in 2D, 12 in 3D, symmetric: V = -V) and its non-negative
+ * weights gamma_z(e) by lattice basis reduction (Sec. 2), and applies the
+ * symmetric, matrix-free operator
+ *
+ *     A u = (1/2) grad E_h(u),   E_h(u) = sum_z sum_{e in V(z)} gamma_z(e) (u(z+e) - u(z))^2
+ *
+ * (Eq. def:E*, grid step h = 1) in explicit Euler steps u <- u - dt A u
+ * (Sec. 4.4) and implicit steps (I + dt A) x = b solved by conjugate
+ * gradients (Sec. 4.2, Eq. elliptic).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are device pointers owned by the caller, contiguous, row-major
+ *    with x fastest: point (x, y[, z]) is element x + n0 (y + n1 z).
+ *  - Work is enqueued on the given CUDA stream and is asynchronous unless the
+ *    entry point says otherwise; buffers must stay alive until it completes.
+ *  - Every entry point returns an adlbr_status; no exception or abort crosses
+ *    the ABI.  adlbr_last_error() gives a message for the calling thread.
+ *  - The library owns the storage behind an adlbr_stencils handle.
+ *  - Offsets and weights are bit-exact functions of D: offsets are exactly
+ *    those of an exactly D-obtuse superbase (every decision is the exact
+ *    sign of a sum of integer multiples of D's entries), put in a canonical
+ *    order and sign (see adlbr_stencils_export).
+ */
+#ifndef ADLBR_H
+#define ADLBR_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADLBR_OK = 0,
+    ADLBR_E_ARG = 1,           /* null pointer, bad enum, bad scalar */
+    ADLBR_E_SHAPE = 2,         /* bad grid extents or mismatched handles */
+    ADLBR_E_NOT_SPD = 3,       /* some D(z) is not symmetric positive definite */
+    ADLBR_E_NONFINITE = 4,     /* some D(z) has a NaN or infinite entry */
+    ADLBR_E_NOT_CONVERGED = 5, /* iteration limit reached (CG, reduction) */
+    ADLBR_E_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    ADLBR_E_CUDA = 7,          /* a CUDA runtime call failed */
+    ADLBR_E_RANGE = 8,         /* an offset does not fit the stencil format */
+    ADLBR_E_INTERNAL = 9
+} adlbr_status;
+
+typedef enum { ADLBR_F64 = 0, ADLBR_F32 = 1, ADLBR_F16 = 2, ADLBR_BF16 = 3 } adlbr_dtype;
+
+/* Boundary rule (Sec. 1): NEUMANN drops every pair (z, z+e) with z+e outside
+ * the grid, V(z; h) = {e in V(z) : z + h e in Omega_h}; PERIODIC wraps. */
+typedef enum { ADLBR_NEUMANN = 0, ADLBR_PERIODIC = 1 } adlbr_boundary;
+
+typedef struct {
+    int32_t dim;   /* 2 or 3 */
+    int32_t bc;    /* adlbr_boundary */
+    int64_t n[3];  /* extents; n[0] is x (fastest); n[2] ignored when dim == 2 */
+} adlbr_grid;
+
+typedef struct adlbr_stencils adlbr_stencils; /* opaque, library-owned */
+
+/* Library version string. */
+const char *adlbr_version(void);
+
+/* Message describing the last non-OK status returned on the calling thread. */
+const char *adlbr_last_error(void);
+
+/*
+ * adlbr_build_stencils -- the AD-LBR stencils of Sec. 2 at every grid point.
+ *
+ * 2D (Sec. 2, Eq. GaussAlgo and the construction after Corollary
+ * ObtuseSuperBaseFromReducedBasis2; Eqs. def:Vz, def:GammaZ): a reduced basis
+ * (e, f) for M ~ adj(D), f negated so that <e, M f> <= 0, superbase
+ * (e0, e1, e2) = (e, f, -e-f), V = {+-e_i}, gamma(+-e_i) =
+ * -<e_{i+1}^perp, D e_{i+2}^perp>/2.
+ * 3D (Sec. 2, Def. ReducedBasis, Prop. MakeObtuse, Lemma Selling / Eq.
+ * DSum3D): a D-obtuse superbase (e0..e3), V = {e_k x e_l}, gamma(e_k x e_l) =
+ * -<e_i, D e_j>/2 for {i,j,k,l} = {0,1,2,3}.
+ *
+ *  g     grid (dim 2 or 3, boundary rule used by later applies).
+ *  D     device, D_t elements: 2D three planes (Dxx, Dxy, Dyy), 3D six planes
+ *        (Dxx, Dyy, Dzz, Dxy, Dxz, Dyz); plane k starts at element k * N,
+ *        N = number of grid points.  D_t is ADLBR_F64 or ADLBR_F32.
+ *  w_t   storage type of the weights: ADLBR_F64, ADLBR_F32 or ADLBR_F16 (F16
+ *        keeps a per-point power-of-two scale, so small weights do not
+ *        underflow).
+ *  out   *out == NULL: a new handle is allocated (cudaMalloc) and returned.
+ *        *out != NULL: must be a handle made for the same grid and w_t; it
+ *        is rebuilt in place with no allocation (usable inside CUDA graphs).
+ *
+ * Points whose tensor is not SPD or not finite, or whose offsets leave the
+ * storage range (|coordinate| > 2047 in 2D, > 127 for the 3D superbase),
+ * get an all-zero stencil and set a sticky error flag in the handle; the
+ * call itself does not synchronise.  adlbr_stencils_check() reports it.
+ */
+adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
+                                  adlbr_dtype w_t, adlbr_stencils **out, cudaStream_t stream);
+
+/* Synchronises `stream`, returns the handle's sticky build status
+ * (ADLBR_OK, ADLBR_E_NONFINITE, ADLBR_E_NOT_SPD, ADLBR_E_RANGE,
+ * ADLBR_E_NOT_CONVERGED) and clears it. */
+adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream);
+
+/* Grid of a handle. */
+adlbr_status adlbr_stencils_grid(const adlbr_stencils *s, adlbr_grid *g);
+
+/*
+ * adlbr_stencils_export -- the canonical half-stencil of every point.
+ *
+ *  offs  device int16 [N][K][dim], K = 3 (2D) or 6 (3D): the offsets of
+ *        V(z) / {+-1}; an offset whose weight is exactly zero is written as
+ *        the zero vector; every other offset has its first non-zero
+ *        coordinate (x, then y, then z) positive; the K pairs are sorted
+ *        lexicographically on (x, y[, z]).
+ *  w     device [N][K] weights gamma_z(+-e) in the same order: double when
+ *        the handle stores F64 weights, float otherwise (F16 storage is
+ *        widened exactly).
+ */
+adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void *w,
+                                   cudaStream_t stream);
+
+adlbr_status adlbr_stencils_destroy(adlbr_stencils *s);
+
+/*
+ * adlbr_apply -- Au = A u with A = (1/2) grad E_h (Eq. def:E*, h = 1):
+ *   (Au)(z) = sum_{e in V(z)} gamma_z(e) (u(z) - u(z+e))
+ *           + sum_{(y, e): e in V(y), y + e = z} gamma_y(e) (u(z) - u(y)),
+ * pairs leaving the grid dropped (NEUMANN) or wrapped (PERIODIC).
+ *
+ *  u    device, N elements of u_t (F64, F32, F16 or BF16).
+ *  Au   device, N elements: double when u_t == ADLBR_F64, float otherwise
+ *       (accumulation is in that type).  Must not alias u.
+ */
+adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
+                         cudaStream_t stream);
+
+/* Bytes of scratch that adlbr_step_explicit needs for u_t. */
+size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t);
+
+/*
+ * adlbr_step_explicit -- nsteps explicit Euler steps of Sec. 4.4,
+ * (u^{n+1} - u^n)/dt = div(D grad u^n), i.e. u <- u - dt A u, in place.
+ *
+ *  u        device, N elements of u_t; the result overwrites it.  For F16 and
+ *           BF16 the update is computed in FP32 and rounded once per step.
+ *  scratch  device, adlbr_step_scratch_bytes(s, u_t) bytes, caller-owned.
+ *  dt       time step; the scheme is monotone for dt <= 1 / max_z A_zz.
+ */
+adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch, adlbr_dtype u_t,
+                                 double dt, int nsteps, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADLBR_H */

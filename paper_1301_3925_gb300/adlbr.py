@@ -1,0 +1,147 @@
+"""Thin ctypes binding of libadlbr.so (include/adlbr.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, converts torch tensors (or raw integer addresses) to device
+pointers and the stream to a cudaStream_t, and raises AdlbrError on a non-OK
+status.  All computation happens in the library's CUDA kernels; there is no
+fallback, and importing the module fails loudly if the library is missing.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadlbr.so")
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+NEUMANN, PERIODIC = 0, 1
+
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_SHAPE", 3: "E_NOT_SPD", 4: "E_NONFINITE",
+          5: "E_NOT_CONVERGED", 6: "E_TIMEOUT", 7: "E_CUDA", 8: "E_RANGE", 9: "E_INTERNAL"}
+
+
+class AdlbrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("bc", ctypes.c_int32), ("n", ctypes.c_int64 * 3)]
+
+
+def grid(shape, bc=NEUMANN):
+    """numpy/torch shape (ny, nx) or (nz, ny, nx) -> adlbr_grid (x fastest)."""
+    g = Grid()
+    g.dim = len(shape)
+    g.bc = bc
+    ext = list(shape)[::-1] + [1] * (3 - len(shape))
+    for k in range(3):
+        g.n[k] = int(ext[k])
+    return g
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libadlbr.so is not built (run paper_1301_3925_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        sigs = {
+            "adlbr_version": (ctypes.c_char_p, []),
+            "adlbr_last_error": (ctypes.c_char_p, []),
+            "adlbr_build_stencils": (_i32, [ctypes.POINTER(Grid), _vp, _i32, _i32,
+                                            ctypes.POINTER(_vp), _vp]),
+            "adlbr_stencils_check": (_i32, [_vp, _vp]),
+            "adlbr_stencils_grid": (_i32, [_vp, ctypes.POINTER(Grid)]),
+            "adlbr_stencils_export": (_i32, [_vp, _vp, _vp, _vp]),
+            "adlbr_stencils_destroy": (_i32, [_vp]),
+            "adlbr_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+            "adlbr_step_scratch_bytes": (ctypes.c_size_t, [_vp, _i32]),
+            "adlbr_step_explicit": (_i32, [_vp, _vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise AdlbrError(st, lib().adlbr_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_code(t):
+    """torch dtype -> adlbr_dtype."""
+    import torch
+    return {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[t]
+
+
+def adlbr_version():
+    return lib().adlbr_version().decode()
+
+
+def adlbr_last_error():
+    return lib().adlbr_last_error().decode(errors="replace")
+
+
+def adlbr_build_stencils(g, D, D_t, w_t, out=None, stream=None):
+    """Returns the stencil handle (an int address); reuses ``out`` if given."""
+    h = _vp(out)
+    _check(lib().adlbr_build_stencils(ctypes.byref(g), _ptr(D), D_t, w_t, ctypes.byref(h),
+                                      _stream(stream)))
+    return h.value
+
+
+def adlbr_stencils_check(h, stream=None):
+    _check(lib().adlbr_stencils_check(h, _stream(stream)))
+
+
+def adlbr_stencils_grid(h):
+    g = Grid()
+    _check(lib().adlbr_stencils_grid(h, ctypes.byref(g)))
+    return g
+
+
+def adlbr_stencils_export(h, offs, w, stream=None):
+    _check(lib().adlbr_stencils_export(h, _ptr(offs), _ptr(w), _stream(stream)))
+
+
+def adlbr_stencils_destroy(h):
+    _check(lib().adlbr_stencils_destroy(h))
+
+
+def adlbr_apply(h, u, Au, u_t, stream=None):
+    _check(lib().adlbr_apply(h, _ptr(u), _ptr(Au), u_t, _stream(stream)))
+
+
+def adlbr_step_scratch_bytes(h, u_t):
+    return int(lib().adlbr_step_scratch_bytes(h, u_t))
+
+
+def adlbr_step_explicit(h, u, scratch, u_t, dt, nsteps, stream=None):
+    _check(lib().adlbr_step_explicit(h, _ptr(u), _ptr(scratch), u_t, float(dt), int(nsteps),
+                                     _stream(stream)))

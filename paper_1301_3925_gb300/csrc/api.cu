@@ -1,0 +1,167 @@
+// C-ABI entry points of libadlbr.so (see include/adlbr.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace adlbr {
+
+static thread_local char g_msg[512] = "";
+
+adlbr_status fail(adlbr_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+adlbr_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(ADLBR_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+adlbr_status check_handle(const adlbr_stencils *s) {
+    if (!s) return fail(ADLBR_E_ARG, "null stencil handle");
+    return ADLBR_OK;
+}
+
+static bool valid_grid(const adlbr_grid *g) {
+    if (!g || (g->dim != 2 && g->dim != 3)) return false;
+    if (g->bc != ADLBR_NEUMANN && g->bc != ADLBR_PERIODIC) return false;
+    for (int k = 0; k < g->dim; ++k)
+        if (g->n[k] <= 0 || g->n[k] > 65535) return false;
+    return true;
+}
+
+static int64_t npoints(const adlbr_grid *g) {
+    return g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
+}
+
+}  // namespace adlbr
+
+using namespace adlbr;
+
+extern "C" {
+
+const char *adlbr_version(void) { return "adlbr-gb300 0.1 (sm_103a)"; }
+
+const char *adlbr_last_error(void) { return g_msg; }
+
+adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
+                                  adlbr_dtype w_t, adlbr_stencils **out, cudaStream_t stream) {
+    if (!out || !D) return fail(ADLBR_E_ARG, "null argument");
+    if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "invalid grid");
+    if (D_t != ADLBR_F32 && D_t != ADLBR_F64) return fail(ADLBR_E_ARG, "D must be F32 or F64");
+    if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
+        return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
+    adlbr_stencils *s = *out;
+    if (s) {
+        bool same = s->dim == g->dim && s->w_t == w_t && s->n[0] == g->n[0] && s->n[1] == g->n[1] &&
+                    (g->dim == 2 || s->n[2] == g->n[2]);
+        if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type");
+        s->bc = g->bc;
+    } else {
+        s = new (std::nothrow) adlbr_stencils();
+        if (!s) return fail(ADLBR_E_INTERNAL, "out of host memory");
+        s->dim = g->dim;
+        s->bc = g->bc;
+        s->n[0] = g->n[0];
+        s->n[1] = g->n[1];
+        s->n[2] = g->dim == 3 ? g->n[2] : 1;
+        s->N = npoints(g);
+        s->w_t = w_t;
+        cudaGetDevice(&s->device);
+        size_t ob = offs_bytes_per_point(s->dim) * (size_t)s->N;
+        size_t wb = w_bytes_per_point(s->dim, w_t) * (size_t)s->N;
+        cudaError_t e = cudaMalloc(&s->offs, ob);
+        if (e == cudaSuccess) e = cudaMalloc(&s->w, wb);
+        if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&s->err_host, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            adlbr_stencils_destroy(s);
+            return cuda_fail(e, "allocating stencil storage");
+        }
+    }
+    adlbr_status st = s->dim == 2 ? launch_build2d(s, D, D_t, stream) : launch_build3d(s, D, D_t, stream);
+    if (st != ADLBR_OK) {
+        if (!*out) adlbr_stencils_destroy(s);
+        return st;
+    }
+    *out = s;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    ADLBR_CUDA(cudaMemcpyAsync(s->err_host, s->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    ADLBR_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), stream));
+    ADLBR_CUDA(cudaStreamSynchronize(stream));
+    int bits = *s->err_host;
+    if (bits & ERRBIT_NONFINITE) return fail(ADLBR_E_NONFINITE, "non-finite tensor entries");
+    if (bits & ERRBIT_NOT_SPD) return fail(ADLBR_E_NOT_SPD, "tensor not positive definite");
+    if (bits & ERRBIT_RANGE) return fail(ADLBR_E_RANGE, "stencil offset out of storage range");
+    if (bits & ERRBIT_NOT_CONVERGED) return fail(ADLBR_E_NOT_CONVERGED, "reduction did not converge");
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_stencils_grid(const adlbr_stencils *s, adlbr_grid *g) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!g) return fail(ADLBR_E_ARG, "null grid");
+    g->dim = s->dim;
+    g->bc = s->bc;
+    g->n[0] = s->n[0];
+    g->n[1] = s->n[1];
+    g->n[2] = s->n[2];
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void *w,
+                                   cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!offs || !w) return fail(ADLBR_E_ARG, "null output");
+    return launch_export(s, offs, w, stream);
+}
+
+adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
+    if (!s) return ADLBR_OK;
+    if (s->offs) cudaFree(s->offs);
+    if (s->w) cudaFree(s->w);
+    if (s->err) cudaFree(s->err);
+    if (s->err_host) cudaFreeHost(s->err_host);
+    if (s->ws) cudaFree(s->ws);
+    delete s;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
+                         cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!u || !Au) return fail(ADLBR_E_ARG, "null vector");
+    if (u == Au) return fail(ADLBR_E_ARG, "Au must not alias u");
+    return launch_apply(s, u, Au, u_t, stream);
+}
+
+size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t) {
+    if (!s) return 0;
+    return (size_t)s->N * (u_t == ADLBR_F64 ? sizeof(double) : sizeof(float));
+}
+
+adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch, adlbr_dtype u_t,
+                                 double dt, int nsteps, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
+    if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
+    for (int k = 0; k < nsteps; ++k) {
+        // scratch <- A u (zeroed by the previous update or by the apply's memset)
+        if (adlbr_status st = launch_apply(s, u, scratch, u_t, stream)) return st;
+        if (adlbr_status st = launch_axpy_zero(s, u, scratch, u_t, dt, stream)) return st;
+    }
+    return ADLBR_OK;
+}
+
+}  // extern "C"

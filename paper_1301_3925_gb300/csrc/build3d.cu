@@ -1,0 +1,263 @@
+// 3D AD-LBR stencil construction, one thread per grid point.
+//
+// Sec. 2 of the paper: a D-reduced basis (Def. ReducedBasis, obtained with
+// the greedy extension of Lagrange's algorithm to d = 3 that the paper
+// cites), Prop. MakeObtuse (Eqs. SignedOrderedIneq, 3DSuperBase) for a
+// D-obtuse superbase (e0, e1, e2, e3), and Selling's stencil (Lemma Selling,
+// Eq. DSum3D): offsets e_k x e_l with weights -<e_i, D e_j>/2.
+//
+// GPU design, as in 2D: the reduction and MakeObtuse run in FP32 on a
+// rescaled D; the resulting superbase is certified with exact signs of the
+// six products <e_i, D e_j> (exact.cuh) and repaired, while a product is
+// positive, by Selling steps (e_i, e_j, e_k, e_l) -> (-e_i, e_j, e_k + e_i,
+// e_l + e_i), each lowering sum |e|_D^2 by 2 <e_i, D e_j>.  The certified
+// superbase is exactly D-obtuse.
+#include "exact.cuh"
+#include "internal.cuh"
+#include "store.cuh"
+
+namespace adlbr {
+
+namespace {
+
+struct V3 {
+    int x, y, z;
+};
+
+__device__ __forceinline__ V3 add(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 neg(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 mul(int k, V3 a) { return V3{k * a.x, k * a.y, k * a.z}; }
+__device__ __forceinline__ int amax(V3 a) { return max(abs(a.x), max(abs(a.y), abs(a.z))); }
+
+// d = (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ float g3(const float (&d)[6], V3 u, V3 v) {
+    float ux = u.x, uy = u.y, uz = u.z, vx = v.x, vy = v.y, vz = v.z;
+    return d[0] * ux * vx + d[1] * uy * vy + d[2] * uz * vz + d[3] * (ux * vy + uy * vx) +
+           d[4] * (ux * vz + uz * vx) + d[5] * (uy * vz + uz * vy);
+}
+
+template <typename T>
+__device__ __forceinline__ void terms3(const T (&D)[6], V3 u, V3 v, T (&x)[6], int (&n)[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) x[k] = D[k];
+    n[0] = u.x * v.x;
+    n[1] = u.y * v.y;
+    n[2] = u.z * v.z;
+    n[3] = u.x * v.y + u.y * v.x;
+    n[4] = u.x * v.z + u.z * v.x;
+    n[5] = u.y * v.z + u.z * v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ int sgnD(const T (&D)[6], V3 u, V3 v) {
+    T x[6];
+    int n[6];
+    terms3(D, u, v, x, n);
+    return exact_sign<6>(x, n);
+}
+
+__device__ __forceinline__ bool finite(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+constexpr int kMaxCoord = 127;
+
+// Lagrange reduction of (e, f) for the FP32 form d; on exit |e| <= |f|.
+__device__ __forceinline__ void lagrange_f(const float (&d)[6], V3 &e, V3 &f) {
+    for (int it = 0; it < 48; ++it) {
+        float den = g3(d, f, f);
+        if (!(den > 0.f)) break;
+        float r = rintf(g3(d, e, f) / den);
+        r = fminf(fmaxf(r, -256.f), 256.f);
+        V3 nf = sub(e, mul((int)r, f));
+        e = f;
+        f = nf;
+        if (amax(f) > 4 * kMaxCoord) break;
+        if (!(g3(d, e, e) > g3(d, f, f))) break;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__restrict__ Dp,
+                                                      char4 *__restrict__ offs, void *wbase,
+                                                      adlbr_dtype wt, int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    T D[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) D[k] = Dp[(int64_t)k * N + i];
+    double wz[6] = {0, 0, 0, 0, 0, 0};
+
+    int code = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (!finite(D[k])) code = ERRBIT_NONFINITE;
+    if (!code) {
+        // leading principal minors with a relative margin
+        double a = D[0], b = D[1], c = D[2], xy = D[3], xz = D[4], yz = D[5];
+        double m2 = a * b - xy * xy;
+        double det = a * (b * c - yz * yz) - xy * (xy * c - yz * xz) + xz * (xy * yz - b * xz);
+        if (!(a > 0.0) || !(b > 0.0) || !(c > 0.0) || !(m2 > 1e-14 * a * b) ||
+            !(det > 1e-13 * a * b * c))
+            code = ERRBIT_NOT_SPD;
+    }
+    char4 *o = offs + 3 * i;
+    if (code) {
+        o[0] = o[1] = o[2] = make_char4(0, 0, 0, 0);
+        store_weights<6>(wbase, wt, i, wz, 63u);
+        atomicOr(err, code);
+        return;
+    }
+
+    // ---- approximate greedy reduction (FP32) ----
+    const double scl = 1.0 / fmax((double)D[0], fmax((double)D[1], (double)D[2]));
+    float d[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = (float)((double)D[k] * scl);
+    V3 b[3] = {V3{1, 0, 0}, V3{0, 1, 0}, V3{0, 0, 1}};
+    for (int it = 0; it < 24; ++it) {
+        // sort by norm
+        float nb[3] = {g3(d, b[0], b[0]), g3(d, b[1], b[1]), g3(d, b[2], b[2])};
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2 - p; ++q)
+                if (nb[q + 1] < nb[q]) {
+                    float tn = nb[q];
+                    nb[q] = nb[q + 1];
+                    nb[q + 1] = tn;
+                    V3 tv = b[q];
+                    b[q] = b[q + 1];
+                    b[q + 1] = tv;
+                }
+        V3 e = b[1], f = b[0];
+        lagrange_f(d, e, f);
+        b[0] = e;
+        b[1] = f;
+        // closest vector to b2 in b0 Z + b1 Z
+        float G00 = g3(d, b[0], b[0]), G01 = g3(d, b[0], b[1]), G11 = g3(d, b[1], b[1]);
+        float r0 = g3(d, b[0], b[2]), r1 = g3(d, b[1], b[2]);
+        float det = G00 * G11 - G01 * G01;
+        if (!(det > 0.f)) break;
+        float y0 = (G11 * r0 - G01 * r1) / det, y1 = (G00 * r1 - G01 * r0) / det;
+        y0 = fminf(fmaxf(y0, -512.f), 512.f);
+        y1 = fminf(fmaxf(y1, -512.f), 512.f);
+        int f0 = (int)floorf(y0), f1 = (int)floorf(y1);
+        V3 best{0, 0, 0};
+        float bestn = 3.4e38f;
+        for (int k0 = f0 - 1; k0 <= f0 + 2; ++k0)
+            for (int k1 = f1 - 1; k1 <= f1 + 2; ++k1) {
+                V3 c = add(mul(k0, b[0]), mul(k1, b[1]));
+                V3 t = sub(b[2], c);
+                float nt = g3(d, t, t);
+                if (nt < bestn) {
+                    bestn = nt;
+                    best = c;
+                }
+            }
+        b[2] = sub(b[2], best);
+        if (amax(b[2]) > 4 * kMaxCoord) break;
+        if (g3(d, b[2], b[2]) >= g3(d, b[1], b[1])) break;
+    }
+
+    // ---- Prop. MakeObtuse (approximate decisions) ----
+    float p01 = fabsf(g3(d, b[0], b[1])), p02 = fabsf(g3(d, b[0], b[2])), p12 = fabsf(g3(d, b[1], b[2]));
+    // the pair with the smallest |<.,D.>| is {b'1, b'2}; b'3 is the other vector,
+    // b'2 the one of the pair whose product with b'3 is larger
+    int i1, i2, i3;
+    if (p01 <= p02 && p01 <= p12) {
+        i3 = 2;
+        if (p02 <= p12) { i1 = 0; i2 = 1; } else { i1 = 1; i2 = 0; }
+    } else if (p02 <= p12) {
+        i3 = 1;
+        if (p01 <= p12) { i1 = 0; i2 = 2; } else { i1 = 2; i2 = 0; }
+    } else {
+        i3 = 0;
+        if (p01 <= p02) { i1 = 1; i2 = 2; } else { i1 = 2; i2 = 1; }
+    }
+    V3 b1 = b[i1], b2 = b[i2], b3 = b[i3];
+    if (g3(d, b1, b3) > 0.f) b1 = neg(b1);
+    if (g3(d, b2, b3) > 0.f) b2 = neg(b2);
+    V3 e[4];
+    if (g3(d, b1, b2) <= 0.f) {
+        e[1] = b1;
+        e[2] = b2;
+        e[3] = b3;
+        e[0] = neg(add(add(b1, b2), b3));
+    } else {
+        e[1] = neg(b1);
+        e[2] = b2;
+        e[3] = add(b1, b3);
+        e[0] = neg(add(b2, b3));
+    }
+
+    // ---- certification with exact signs, Selling repair ----
+    // pair q = (i, j), complement (k, l)
+    constexpr int PI[6] = {0, 0, 0, 1, 1, 2};
+    constexpr int PJ[6] = {1, 2, 3, 2, 3, 3};
+    constexpr int PK[6] = {2, 1, 1, 0, 0, 0};
+    constexpr int PL[6] = {3, 3, 2, 3, 2, 1};
+    int sg[6];
+    bool ok = false, range = false;
+    for (int fix = 0; fix < 256; ++fix) {
+        range = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) range |= amax(e[k]) > kMaxCoord;
+        if (range) break;
+        int bad = -1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            sg[q] = sgnD(D, e[PI[q]], e[PJ[q]]);
+            if (sg[q] > 0 && bad < 0) bad = q;
+        }
+        if (bad < 0) {
+            ok = true;
+            break;
+        }
+        const int ii = PI[bad], kk = PK[bad], ll = PL[bad];
+        V3 ei = e[ii];
+        e[ii] = neg(ei);
+        e[kk] = add(e[kk], ei);
+        e[ll] = add(e[ll], ei);
+    }
+    if (!ok) {
+        o[0] = o[1] = o[2] = make_char4(0, 0, 0, 0);
+        store_weights<6>(wbase, wt, i, wz, 63u);
+        atomicOr(err, range ? ERRBIT_RANGE : ERRBIT_NOT_CONVERGED);
+        return;
+    }
+
+    unsigned zmask = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        if (sg[q] == 0) {
+            zmask |= 1u << q;
+        } else {
+            T x[6];
+            int n[6];
+            terms3(D, e[PI[q]], e[PJ[q]], x, n);
+            wz[q] = fmax(-0.5 * accurate_value<6>(x, n), 0.0);
+        }
+    }
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        o[k - 1] = make_char4((signed char)e[k].x, (signed char)e[k].y, (signed char)e[k].z, 0);
+    store_weights<6>(wbase, wt, i, wz, zmask);
+}
+
+}  // namespace
+
+adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st) {
+    const int threads = 128;
+    unsigned blocks = blocks_for(s->N, threads);
+    if (D_t == ADLBR_F32)
+        build3d_kernel<float><<<blocks, threads, 0, st>>>(s->N, (const float *)D, (char4 *)s->offs,
+                                                          s->w, s->w_t, s->err);
+    else
+        build3d_kernel<double><<<blocks, threads, 0, st>>>(s->N, (const double *)D,
+                                                           (char4 *)s->offs, s->w, s->w_t, s->err);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+}  // namespace adlbr

@@ -1,0 +1,167 @@
+// Exact signs and accurate values of sum_k n_k x_k (small integers n_k,
+// floating-point x_k) on the device.
+//
+// Every decision of the stencil construction is such a sign.  The common
+// case is settled by a filter: the sum evaluated in FP32 (FP64 for FP64
+// inputs) together with a forward error bound; only when the computed value
+// lies within the bound (ties and near-ties) the sum is evaluated exactly as
+// a floating-point expansion, accumulated with Shewchuk's Grow-Expansion
+// (J. R. Shewchuk, "Adaptive precision floating-point arithmetic and fast
+// robust geometric predicates", 1997) over error-free products.  For FP32
+// inputs every product n_k * x_k is exact in FP64 (24-bit mantissa times an
+// integer below 2^24); for FP64 inputs each product is split by an fma into
+// two doubles.  All arithmetic uses explicitly rounded intrinsics so that no
+// contraction can change it.
+#pragma once
+
+#include <stdint.h>
+
+namespace adlbr {
+
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+
+// Adds b to the non-overlapping expansion h[0..m) (increasing magnitude).
+__device__ __forceinline__ int grow_expansion(double *h, int m, double b) {
+    double q = b;
+    int mm = 0;
+    for (int i = 0; i < m; ++i) {
+        double s, e;
+        two_sum_d(q, h[i], s, e);
+        q = s;
+        if (e != 0.0) h[mm++] = e;
+    }
+    if (q != 0.0) h[mm++] = q;
+    return mm;
+}
+
+// ---- FP32 inputs, |n_k| < 2^24 -------------------------------------------
+template <int K>
+__device__ __noinline__ int exact_sign_slow_f32(const float (&x)[K], const int (&n)[K]) {
+    double h[K + 1];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) m = grow_expansion(h, m, __dmul_rn((double)n[k], (double)x[k]));
+    return m == 0 ? 0 : (h[m - 1] > 0.0 ? 1 : -1);
+}
+
+template <int K>
+__device__ __forceinline__ int exact_sign_f32(const float (&x)[K], const int (&n)[K]) {
+    float v = 0.f, A = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float p = __fmul_rn((float)n[k], x[k]);
+        v = __fadd_rn(v, p);
+        A = __fadd_rn(A, fabsf(p));
+    }
+    if (A == 0.f) return 0;
+    // |v - exact| <= (2K) u A (1 + small); take a factor-2 margin and an
+    // absolute term for underflowing products.
+    float bound = __fmaf_rn(A, (float)(4 * K + 4) * 0x1p-24f, 0x1p-120f);
+    if (fabsf(v) > bound) return v > 0.f ? 1 : -1;
+    return exact_sign_slow_f32<K>(x, n);
+}
+
+// Nearly correctly rounded value (float-float accumulation of exact products).
+template <int K>
+__device__ __forceinline__ float accurate_value_f32(const float (&x)[K], const int (&n)[K]) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float nk = (float)n[k];
+        float p = __fmul_rn(nk, x[k]);
+        float pe = __fmaf_rn(nk, x[k], -p);
+        float t = __fadd_rn(s, p);
+        float bv = __fsub_rn(t, s);
+        float av = __fsub_rn(t, bv);
+        float err = __fadd_rn(__fsub_rn(s, av), __fsub_rn(p, bv));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, pe));
+    }
+    return __fadd_rn(s, c);
+}
+
+// ---- FP64 inputs, |n_k| < 2^31 -------------------------------------------
+template <int K>
+__device__ __noinline__ int exact_sign_slow_f64(const double (&x)[K], const int (&n)[K]) {
+    double h[2 * K + 1];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double nk = (double)n[k];
+        double p = __dmul_rn(nk, x[k]);
+        double pe = __fma_rn(nk, x[k], -p);
+        m = grow_expansion(h, m, pe);
+        m = grow_expansion(h, m, p);
+    }
+    return m == 0 ? 0 : (h[m - 1] > 0.0 ? 1 : -1);
+}
+
+template <int K>
+__device__ __forceinline__ int exact_sign_f64(const double (&x)[K], const int (&n)[K]) {
+    double v = 0.0, A = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double p = __dmul_rn((double)n[k], x[k]);
+        v = __dadd_rn(v, p);
+        A = __dadd_rn(A, fabs(p));
+    }
+    if (A == 0.0) return 0;
+    double bound = __fma_rn(A, (double)(4 * K + 4) * 0x1p-53, 0x1p-1000);
+    if (fabs(v) > bound) return v > 0.0 ? 1 : -1;
+    return exact_sign_slow_f64<K>(x, n);
+}
+
+template <int K>
+__device__ __forceinline__ double accurate_value_f64(const double (&x)[K], const int (&n)[K]) {
+    double s = 0.0, c = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double nk = (double)n[k];
+        double p = __dmul_rn(nk, x[k]);
+        double pe = __fma_rn(nk, x[k], -p);
+        double t, err;
+        two_sum_d(s, p, t, err);
+        s = t;
+        c = __dadd_rn(c, __dadd_rn(err, pe));
+    }
+    return __dadd_rn(s, c);
+}
+
+// Dispatch on the input type.
+template <int K>
+__device__ __forceinline__ int exact_sign(const float (&x)[K], const int (&n)[K]) {
+    return exact_sign_f32<K>(x, n);
+}
+template <int K>
+__device__ __forceinline__ int exact_sign(const double (&x)[K], const int (&n)[K]) {
+    return exact_sign_f64<K>(x, n);
+}
+template <int K>
+__device__ __forceinline__ double accurate_value(const float (&x)[K], const int (&n)[K]) {
+    // float-float accumulation, returned as its (double) sum
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float nk = (float)n[k];
+        float p = __fmul_rn(nk, x[k]);
+        float pe = __fmaf_rn(nk, x[k], -p);
+        float t = __fadd_rn(s, p);
+        float bv = __fsub_rn(t, s);
+        float av = __fsub_rn(t, bv);
+        float err = __fadd_rn(__fsub_rn(s, av), __fsub_rn(p, bv));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, pe));
+    }
+    return __dadd_rn((double)s, (double)c);
+}
+template <int K>
+__device__ __forceinline__ double accurate_value(const double (&x)[K], const int (&n)[K]) {
+    return accurate_value_f64<K>(x, n);
+}
+
+}  // namespace adlbr

@@ -1,0 +1,142 @@
+"""Parity of the CUDA operator and explicit step with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1301_3925_gb300 import adlbr as ab
+
+from gpu_helpers import build, dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_apply(h, u_np, u_dtype):
+    t = torch()
+    u = dev(u_np.ravel(), u_dtype)
+    acc = t.float64 if u_dtype == t.float64 else t.float32
+    Au = t.empty(u.numel(), dtype=acc, device="cuda")
+    ab.adlbr_apply(h, u, Au, ab.dtype_code(u_dtype))
+    t.cuda.synchronize()
+    return Au.double().cpu().numpy().reshape(u_np.shape), u.double().cpu().numpy().reshape(u_np.shape)
+
+
+def _oracle_stencils(seen, dim):
+    if dim == 2:
+        oo, ow, st, _ = oracle.build2d(*seen.reshape(3, -1))
+    else:
+        oo, ow, st, _ = oracle.build3d(seen.reshape(6, -1))
+    assert np.all(st == 0)
+    return oo, ow
+
+
+@pytest.mark.parametrize("bc", [ab.NEUMANN, ab.PERIODIC])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_apply_fp64(bc, dim):
+    t = torch()
+    if dim == 2:
+        shape = (45, 67)
+        D = synth.smooth_field2d(*shape, seed=3, kappa_min=1, kappa_max=60, lattice=6)
+    else:
+        shape = (13, 17, 19)
+        D = synth.needle_field3d(19, seed=5, kappa=15.0)[:, :13, :17, :19]
+    h, seen, _ = build(D, shape, t.float64, ab.F64, bc)
+    try:
+        u = synth.u_uniform(shape, 1)
+        Au, _ = _gpu_apply(h, u, t.float64)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    oo, ow = _oracle_stencils(seen, dim)
+    ref = oracle.apply(shape, bc, oo, ow, u)
+    assert np.abs(Au - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_apply_fp32_within_1e5(dim):
+    """FP32 u, FP32 weights, FP32 accumulation: relative L-inf error <= 1e-5."""
+    t = torch()
+    if dim == 2:
+        shape = (64, 96)
+        D = synth.smooth_field2d(*shape, seed=4, kappa_min=1, kappa_max=100, lattice=8)
+    else:
+        shape = (20, 24, 28)
+        D = synth.needle_field3d(28, seed=6, kappa=20.0)[:, :20, :24, :28]
+    h, seen, _ = build(D, shape, t.float32, ab.F32)
+    try:
+        u = synth.u_uniform(shape, 2)
+        Au, useen = _gpu_apply(h, u, t.float32)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    oo, ow = _oracle_stencils(seen, dim)
+    ref = oracle.apply(shape, ab.NEUMANN, oo, ow, useen)
+    assert np.abs(Au - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_explicit_64x64_fp64_10_steps():
+    """64x64 FP64, spiral field kappa = 10, u0 ~ U[0,1] (seed 0), 10 explicit
+    steps at dt = 1 / max A_zz, zero-flux boundary: GPU == oracle to 1e-12."""
+    t = torch()
+    D = synth.spiral_field(64, 10.0)
+    h, seen, _ = build(D, (64, 64), t.float64, ab.F64)
+    oo, ow = _oracle_stencils(seen, 2)
+    dt = oracle.dt_limit((64, 64), oracle.NEUMANN, oo, ow)
+    u0 = synth.u_uniform((64, 64), 0)
+    try:
+        u = dev(u0.ravel(), t.float64)
+        scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.F64), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(h, u, scratch, ab.F64, dt, 10)
+        t.cuda.synchronize()
+        ug = u.cpu().numpy().reshape(64, 64)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    ref = oracle.step_explicit((64, 64), oracle.NEUMANN, oo, ow, u0, dt, 10)
+    assert np.abs(ug - ref).max() <= 1e-12 * np.abs(ref).max()
+    # discrete maximum principle and mass conservation hold on the GPU too
+    assert ug.min() >= u0.min() - 1e-12 and ug.max() <= u0.max() + 1e-12
+    assert abs(ug.sum() - u0.sum()) <= 1e-9
+
+
+@pytest.mark.parametrize("u_name,w_t,tol", [("float32", ab.F32, 1e-5), ("float32", ab.F16, 1e-3),
+                                            ("bfloat16", ab.F16, 2e-2), ("float16", ab.F16, 4e-3)])
+def test_explicit_step_error_per_step(u_name, w_t, tol):
+    """Per-step relative L-inf error of one explicit step from the same u^n,
+    against the FP64 oracle fed the same (rounded) u^n and D."""
+    t = torch()
+    shape = (96, 128)
+    D = synth.smooth_field2d(*shape, seed=8, kappa_min=1, kappa_max=100, lattice=8)
+    h, seen, _ = build(D, shape, t.float32, w_t)
+    oo, ow = _oracle_stencils(seen, 2)
+    dt = oracle.dt_limit(shape, oracle.NEUMANN, oo, ow)
+    u0 = synth.u_uniform(shape, 3)
+    ud = getattr(t, u_name)
+    try:
+        u = dev(u0.ravel(), ud)
+        useen = u.double().cpu().numpy().reshape(shape)
+        scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.dtype_code(ud)), dtype=t.uint8,
+                          device="cuda")
+        ab.adlbr_step_explicit(h, u, scratch, ab.dtype_code(ud), dt, 1)
+        t.cuda.synchronize()
+        ug = u.double().cpu().numpy().reshape(shape)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    ref = oracle.step_explicit(shape, oracle.NEUMANN, oo, ow, useen, dt, 1)
+    err = np.abs(ug - ref).max() / np.abs(ref).max()
+    assert err <= tol, err
+
+
+def test_apply_full_size_4096():
+    """4096^2 FP32 field, kappa up to 100 (CED-sized), FP32 weights and u:
+    every output against the oracle, plus Neumann mass conservation."""
+    t = torch()
+    n = 4096
+    D = synth.smooth_field2d(n, n, seed=9, kappa_min=1, kappa_max=100, lattice=64)
+    h, seen, _ = build(D, (n, n), t.float32, ab.F32)
+    try:
+        u = synth.u_uniform((n, n), 4)
+        Au, useen = _gpu_apply(h, u, t.float32)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    oo, ow = _oracle_stencils(seen, 2)
+    ref = oracle.apply((n, n), oracle.NEUMANN, oo, ow, useen)
+    assert np.abs(Au - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert abs(Au.sum()) <= 1e-6 * np.abs(Au).sum()
