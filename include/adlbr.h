@@ -156,6 +156,84 @@ size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t);
 adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch, adlbr_dtype u_t,
                                  double dt, int nsteps, cudaStream_t stream);
 
+/*
+ * adlbr_step_implicit -- one implicit step: solves (I + dt A) x = rhs by
+ * conjugate gradients (the discretised Eq. elliptic of Sec. 4.2 with
+ * lambda = dt, solved by CG as there).  FP32 vectors; every dot product and
+ * norm is accumulated in FP64 with a deterministic reduction; alpha and beta
+ * are computed on the device.  Each round starts from the true residual
+ * rhs - (x + dt A x), evaluated with the operator accumulated in FP64, and
+ * runs CG until the recursively updated residual satisfies
+ * |r| <= rtol |rhs|; a new round (iterative refinement) follows while the
+ * true residual is above rtol and still halves per round.  Because x is
+ * stored in FP32, the true residual cannot go much below
+ * eps_32 |I + dt A| (a few 1e-6 at dt = 200 times the explicit limit);
+ * relres_out reports it.
+ *
+ *  rhs         device float [N].
+ *  x           device float [N]: initial guess on entry, solution on exit.
+ *  precond     0: plain CG.  1: flexible CG preconditioned by the U-Net of
+ *              adlbr_unet_* with parameters nn (see below).
+ *  nn          preconditioner parameters (precond == 1), else ignored.
+ *  iters_out   iterations performed (may be NULL).
+ *  relres_out  final true relative residual |rhs - (I + dt A) x| / |rhs|.
+ * The first call on a handle allocates its solver workspace (cudaMalloc);
+ * later calls reuse it.  Synchronises the stream every few iterations.
+ * Returns ADLBR_E_NOT_CONVERGED if maxit is reached first.
+ */
+adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, double dt,
+                                 double rtol, int maxit, int precond, const void *nn,
+                                 int *iters_out, double *relres_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Coherence-enhancing diffusion (Sec. 4.4, Eq. parabolique), 2D, FP32.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of scratch for adlbr_ced_tensor / adlbr_ced_step on grid g. */
+size_t adlbr_ced_scratch_bytes(const adlbr_grid *g);
+
+/*
+ * adlbr_ced_tensor -- the diffusion tensor D(J_rho(grad u_sigma)) of Sec. 4.4:
+ * u_sigma = K_sigma * u, J_rho = K_rho * (grad u_sigma grad u_sigma^T); D has
+ * the eigenvectors v1, v2 of J_rho (eigenvalues mu1 >= mu2) with eigenvalues
+ * lambda1 = alpha and lambda2 = alpha + (1 - alpha) exp(-C / (mu1 - mu2)^2)
+ * (exp(-C/0) = 0).  sigma, rho: standard deviations of the Gaussians, which
+ * are truncated at radius int(3 s + 0.5) <= 32 and normalised; the image is
+ * reflected about its border (u(-1) = u(0)) for the convolutions and for the
+ * centred-difference gradient.
+ *
+ *  g        2D grid.
+ *  u        device float [N].
+ *  D        device float [3][N]: planes Dxx, Dxy, Dyy (build_stencils input).
+ *  scratch  device, adlbr_ced_scratch_bytes(g) bytes.
+ */
+adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, double sigma,
+                              double rho, double alpha, double C, void *scratch,
+                              cudaStream_t stream);
+
+/*
+ * adlbr_ced_stencils -- the tensor stage of adlbr_ced_tensor fused with
+ * adlbr_build_stencils: the AD-LBR stencils of D(J_rho(grad u_sigma)) are
+ * built from D while it is still on chip (D is not written out).  *s follows
+ * adlbr_build_stencils' rules (allocated when NULL, rebuilt in place
+ * otherwise).  The offsets and weights equal those of adlbr_build_stencils
+ * applied to the D that adlbr_ced_tensor returns, bit for bit.
+ */
+adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const float *u,
+                                void *scratch, double sigma, double rho, double alpha, double C,
+                                adlbr_dtype w_t, cudaStream_t stream);
+
+/*
+ * adlbr_ced_step -- nsteps steps of the CED loop of Sec. 4.4 with a frozen
+ * tensor per step (D_n = D(u(n dt)), Sec. 1): tensor (adlbr_ced_tensor),
+ * stencils (adlbr_build_stencils into *s, allocated on the first call and
+ * rebuilt in place afterwards, weights stored as w_t), one explicit step
+ * u <- u - dt A u.  u is FP32 and updated in place.
+ */
+adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, void *scratch,
+                            double sigma, double rho, double alpha, double C, double dt,
+                            int nsteps, adlbr_dtype w_t, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,18 @@ def lib():
             "adlbr_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
             "adlbr_step_scratch_bytes": (ctypes.c_size_t, [_vp, _i32]),
             "adlbr_step_explicit": (_i32, [_vp, _vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
+            "adlbr_step_implicit": (_i32, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
+                                           _i32, _vp, ctypes.POINTER(_i32),
+                                           ctypes.POINTER(ctypes.c_double), _vp]),
+            "adlbr_ced_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid)]),
+            "adlbr_ced_tensor": (_i32, [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+            "adlbr_ced_stencils": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(Grid), _vp, _vp,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _i32, _vp]),
+            "adlbr_ced_step": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(Grid), _vp, _vp,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, _i32, _i32, _vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -145,3 +157,40 @@ def adlbr_step_scratch_bytes(h, u_t):
 def adlbr_step_explicit(h, u, scratch, u_t, dt, nsteps, stream=None):
     _check(lib().adlbr_step_explicit(h, _ptr(u), _ptr(scratch), u_t, float(dt), int(nsteps),
                                      _stream(stream)))
+
+
+def adlbr_ced_scratch_bytes(g):
+    return int(lib().adlbr_ced_scratch_bytes(ctypes.byref(g)))
+
+
+def adlbr_ced_tensor(g, u, D, sigma, rho, alpha, C, scratch, stream=None):
+    _check(lib().adlbr_ced_tensor(ctypes.byref(g), _ptr(u), _ptr(D), float(sigma), float(rho),
+                                  float(alpha), float(C), _ptr(scratch), _stream(stream)))
+
+
+def adlbr_ced_step(h, g, u, scratch, sigma, rho, alpha, C, dt, nsteps, w_t, stream=None):
+    """Returns the (possibly newly allocated) stencil handle."""
+    hh = _vp(h)
+    _check(lib().adlbr_ced_step(ctypes.byref(hh), ctypes.byref(g), _ptr(u), _ptr(scratch),
+                                float(sigma), float(rho), float(alpha), float(C), float(dt),
+                                int(nsteps), w_t, _stream(stream)))
+    return hh.value
+
+
+def adlbr_ced_stencils(h, g, u, scratch, sigma, rho, alpha, C, w_t, stream=None):
+    """Returns the (possibly newly allocated) stencil handle."""
+    hh = _vp(h)
+    _check(lib().adlbr_ced_stencils(ctypes.byref(hh), ctypes.byref(g), _ptr(u), _ptr(scratch),
+                                    float(sigma), float(rho), float(alpha), float(C), w_t,
+                                    _stream(stream)))
+    return hh.value
+
+
+def adlbr_step_implicit(h, rhs, x, dt, rtol, maxit, precond=0, nn=None, stream=None):
+    """Returns (iterations, true relative residual)."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    _check(lib().adlbr_step_implicit(h, _ptr(rhs), _ptr(x), float(dt), float(rtol), int(maxit),
+                                     int(precond), _ptr(nn), ctypes.byref(it), ctypes.byref(rr),
+                                     _stream(stream)))
+    return it.value, rr.value

@@ -40,6 +40,42 @@ static int64_t npoints(const adlbr_grid *g) {
     return g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
 }
 
+// *ps == NULL: allocates a handle for grid g and weight type w_t.
+// *ps != NULL: checks that it matches (and takes g's boundary rule).
+static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_stencils **ps) {
+    adlbr_stencils *s = *ps;
+    if (s) {
+        bool same = s->dim == g->dim && s->w_t == w_t && s->n[0] == g->n[0] && s->n[1] == g->n[1] &&
+                    (g->dim == 2 || s->n[2] == g->n[2]);
+        if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type");
+        s->bc = g->bc;
+        return ADLBR_OK;
+    }
+    s = new (std::nothrow) adlbr_stencils();
+    if (!s) return fail(ADLBR_E_INTERNAL, "out of host memory");
+    s->dim = g->dim;
+    s->bc = g->bc;
+    s->n[0] = g->n[0];
+    s->n[1] = g->n[1];
+    s->n[2] = g->dim == 3 ? g->n[2] : 1;
+    s->N = npoints(g);
+    s->w_t = w_t;
+    cudaGetDevice(&s->device);
+    size_t ob = offs_bytes_per_point(s->dim) * (size_t)s->N;
+    size_t wb = w_bytes_per_point(s->dim, w_t) * (size_t)s->N;
+    cudaError_t e = cudaMalloc(&s->offs, ob);
+    if (e == cudaSuccess) e = cudaMalloc(&s->w, wb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->err_host, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        adlbr_stencils_destroy(s);
+        return cuda_fail(e, "allocating stencil storage");
+    }
+    *ps = s;
+    return ADLBR_OK;
+}
+
 }  // namespace adlbr
 
 using namespace adlbr;
@@ -58,34 +94,7 @@ adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtyp
     if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
         return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
     adlbr_stencils *s = *out;
-    if (s) {
-        bool same = s->dim == g->dim && s->w_t == w_t && s->n[0] == g->n[0] && s->n[1] == g->n[1] &&
-                    (g->dim == 2 || s->n[2] == g->n[2]);
-        if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type");
-        s->bc = g->bc;
-    } else {
-        s = new (std::nothrow) adlbr_stencils();
-        if (!s) return fail(ADLBR_E_INTERNAL, "out of host memory");
-        s->dim = g->dim;
-        s->bc = g->bc;
-        s->n[0] = g->n[0];
-        s->n[1] = g->n[1];
-        s->n[2] = g->dim == 3 ? g->n[2] : 1;
-        s->N = npoints(g);
-        s->w_t = w_t;
-        cudaGetDevice(&s->device);
-        size_t ob = offs_bytes_per_point(s->dim) * (size_t)s->N;
-        size_t wb = w_bytes_per_point(s->dim, w_t) * (size_t)s->N;
-        cudaError_t e = cudaMalloc(&s->offs, ob);
-        if (e == cudaSuccess) e = cudaMalloc(&s->w, wb);
-        if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
-        if (e == cudaSuccess) e = cudaMallocHost(&s->err_host, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
-        if (e != cudaSuccess) {
-            adlbr_stencils_destroy(s);
-            return cuda_fail(e, "allocating stencil storage");
-        }
-    }
+    if (adlbr_status e = acquire_handle(g, w_t, &s)) return e;
     adlbr_status st = s->dim == 2 ? launch_build2d(s, D, D_t, stream) : launch_build3d(s, D, D_t, stream);
     if (st != ADLBR_OK) {
         if (!*out) adlbr_stencils_destroy(s);
@@ -156,10 +165,87 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
     if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
     if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
+    if (nsteps == 0) return ADLBR_OK;
+    // scratch accumulates dt A u; each finalize pass consumes and re-zeroes it
+    ADLBR_CUDA(cudaMemsetAsync(scratch, 0, adlbr_step_scratch_bytes(s, u_t), stream));
     for (int k = 0; k < nsteps; ++k) {
-        // scratch <- A u (zeroed by the previous update or by the apply's memset)
-        if (adlbr_status st = launch_apply(s, u, scratch, u_t, stream)) return st;
-        if (adlbr_status st = launch_axpy_zero(s, u, scratch, u_t, dt, stream)) return st;
+        if (adlbr_status st = launch_accumulate(s, u, scratch, u_t, dt, nullptr, stream)) return st;
+        if (adlbr_status st = launch_finalize(s, u, scratch, u_t, stream)) return st;
+    }
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, double dt,
+                                 double rtol, int maxit, int precond, const void *nn,
+                                 int *iters_out, double *relres_out, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!rhs || !x) return fail(ADLBR_E_ARG, "null vector");
+    if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
+    if (precond != 0) return fail(ADLBR_E_ARG, "unknown preconditioner %d", precond);
+    (void)nn;
+    return run_cg(s, (const float *)rhs, (float *)x, dt, rtol, maxit, iters_out, relres_out, stream);
+}
+
+size_t adlbr_ced_scratch_bytes(const adlbr_grid *g) {
+    if (!valid_grid(g) || g->dim != 2) return 0;
+    const int64_t N = npoints(g);
+    // tensor temporaries (6N) + D (3N) + step accumulator (N), floats
+    return ced_tensor_scratch_bytes(N) + (size_t)N * sizeof(float) * 4;
+}
+
+adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, double sigma,
+                              double rho, double alpha, double C, void *scratch,
+                              cudaStream_t stream) {
+    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!u || !D || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    return launch_ced_tensor((int)g->n[0], (int)g->n[1], u, D, sigma, rho, alpha, C, scratch, stream);
+}
+
+adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const float *u,
+                                void *scratch, double sigma, double rho, double alpha, double C,
+                                adlbr_dtype w_t, cudaStream_t stream) {
+    if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
+    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
+        return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
+    const int64_t N = npoints(g);
+    float *D = (float *)((char *)scratch + ced_tensor_scratch_bytes(N));
+    const bool fresh = *s == nullptr;
+    if (adlbr_status st = acquire_handle(g, w_t, s)) return st;
+    adlbr_status st = launch_ced_build(*s, u, sigma, rho, alpha, C, scratch, D, stream);
+    if (st != ADLBR_OK && fresh) {
+        adlbr_stencils_destroy(*s);
+        *s = nullptr;
+    }
+    return st;
+}
+
+adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, void *scratch,
+                            double sigma, double rho, double alpha, double C, double dt,
+                            int nsteps, adlbr_dtype w_t, cudaStream_t stream) {
+    if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
+    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
+    const int64_t N = npoints(g);
+    float *D = (float *)((char *)scratch + ced_tensor_scratch_bytes(N));
+    float *acc = D + 3 * N;
+    if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
+        return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
+    const bool fresh = *s == nullptr;
+    if (adlbr_status st = acquire_handle(g, w_t, s)) return st;
+    for (int k = 0; k < nsteps; ++k) {
+        // tensor stage fused with the stencil construction (D kept on chip)
+        adlbr_status st = launch_ced_build(*s, u, sigma, rho, alpha, C, scratch, D, stream);
+        if (st == ADLBR_OK) st = adlbr_step_explicit(*s, u, acc, ADLBR_F32, dt, 1, stream);
+        if (st != ADLBR_OK) {
+            if (fresh) {
+                adlbr_stencils_destroy(*s);
+                *s = nullptr;
+            }
+            return st;
+        }
     }
     return ADLBR_OK;
 }

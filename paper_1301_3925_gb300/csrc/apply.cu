@@ -1,12 +1,18 @@
-// Operator application A u = (1/2) grad E_h(u) (Eq. def:E*, h = 1) and the
-// canonical export of the stencils.
+// Operator application A u = (1/2) grad E_h(u) (Eq. def:E*, h = 1), the
+// explicit step, and the canonical export of the stencils.
 //
 // The operator is a sum over the directed edges (z, e), e in V(z), of
-// gamma_z(e) (u(z) - u(z+e)) added at z and subtracted at z+e.  Scatter
-// formulation: one thread per point z gathers its own edges' contributions
-// into a register and pushes the opposite contributions to the far ends
-// with fire-and-forget atomics (red.global.add), which L2 performs.  Pairs
-// that leave the grid are dropped (Neumann rule of Sec. 1) or wrapped.
+// gamma_z(e) (u(z) - u(z+e)) added at z and subtracted at z+e.  Pairs that
+// leave the grid are dropped (Neumann rule of Sec. 1) or wrapped (periodic).
+//
+// Scatter formulation: one thread per point z accumulates its own edges into
+// a register and pushes the opposite contributions to the far ends.  The 2D
+// kernel for FP32/F16/BF16 vectors stages those pushes in a shared-memory
+// window covering its 64 x 32 tile plus an 8-point halo (95% of the edges of
+// the kappa <= 100 CED stencils are at most 8 points long); only pushes that
+// leave the window go to L2 as scalar reductions, and the window is flushed
+// with coalesced 16-byte vector reductions (red.global.add.v4.f32).
+// The FP64 path and the 3D path push every contribution to L2 directly.
 #include "internal.cuh"
 
 namespace adlbr {
@@ -16,6 +22,14 @@ namespace {
 __device__ __forceinline__ int wrap(int c, int n) {
     c %= n;
     return c < 0 ? c + n : c;
+}
+
+__device__ __forceinline__ void red_add(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
 }
 
 // Selling offsets of a 3D superbase (e0 = -e1-e2-e3): pair q = (i, j) gets
@@ -41,13 +55,96 @@ __device__ __forceinline__ void selling_offsets(const char4 (&b)[3], int (&c)[6]
     }
 }
 
+// ---- 2D, shared-memory window ------------------------------------------
+constexpr int TW = 64, TH = 32, HALO = 8, WW = TW + 2 * HALO, WH = TH + 2 * HALO;
+constexpr int TILE_THREADS = 256;
+
 template <typename UT>
-__global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc,
+__global__ void __launch_bounds__(TILE_THREADS) apply2d_tiled(int nx, int ny, int bc, float scale,
+                                                              const short4 *__restrict__ offs,
+                                                              const void *__restrict__ wbase,
+                                                              adlbr_dtype wt, const UT *__restrict__ u,
+                                                              float *__restrict__ acc,
+                                                              const int *__restrict__ skip) {
+    __shared__ __align__(16) float win[WH * WW];
+    if (skip && *skip) return;
+    for (int c = threadIdx.x; c < WH * WW; c += TILE_THREADS) win[c] = 0.f;
+    __syncthreads();
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int tx = threadIdx.x % TW, ty = threadIdx.x / TW;
+    const int x = x0 + tx;
+    const bool periodic = bc == ADLBR_PERIODIC;
+    if (x < nx) {
+        for (int k = 0; k < TH / (TILE_THREADS / TW); ++k) {
+            const int y = y0 + ty + k * (TILE_THREADS / TW);
+            if (y >= ny) break;
+            const int64_t z = (int64_t)y * nx + x;
+            const short4 o = offs[z];
+            float w[3];
+            load_weights<float, 3>(wbase, wt, z, w);
+            const int ex[3] = {o.x, o.z, -o.x - o.z}, ey[3] = {o.y, o.w, -o.y - o.w};
+            const float uz = to_acc(u[z]);
+            float own = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float wi = scale * w[i];
+                if (wi == 0.f) continue;
+#pragma unroll
+                for (int s = -1; s <= 1; s += 2) {
+                    const int xn = x + s * ex[i], yn = y + s * ey[i];
+                    int xg = xn, yg = yn;
+                    if (periodic) {
+                        xg = wrap(xn, nx);
+                        yg = wrap(yn, ny);
+                    } else if (xn < 0 || xn >= nx || yn < 0 || yn >= ny) {
+                        continue;
+                    }
+                    const int64_t zn = (int64_t)yg * nx + xg;
+                    const float f = wi * (uz - to_acc(u[zn]));
+                    own += f;
+                    const int wx = xn - x0 + HALO, wy = yn - y0 + HALO;
+                    if ((unsigned)wx < (unsigned)WW && (unsigned)wy < (unsigned)WH)
+                        atomicAdd(&win[wy * WW + wx], -f);
+                    else
+                        red_add(acc + zn, -f);
+                }
+            }
+            atomicAdd(&win[(y - y0 + HALO) * WW + tx + HALO], own);
+        }
+    }
+    __syncthreads();
+    // flush the window: 4 consecutive cells per thread and step
+    const bool vec_ok = (nx % 4) == 0;
+    for (int c4 = threadIdx.x; c4 < WH * WW / 4; c4 += TILE_THREADS) {
+        const int wy = c4 / (WW / 4), wx = (c4 % (WW / 4)) * 4;
+        const float4 v = *reinterpret_cast<const float4 *>(&win[wy * WW + wx]);
+        if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+        int gy = y0 - HALO + wy;
+        const int gx = x0 - HALO + wx;
+        if (periodic) gy = wrap(gy, ny);
+        else if (gy < 0 || gy >= ny) continue;
+        if (vec_ok && gx >= 0 && gx + 3 < nx) {
+            red_add_v4(acc + (int64_t)gy * nx + gx, v.x, v.y, v.z, v.w);
+        } else {
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (vv[t] == 0.f) continue;
+                int xx = gx + t;
+                if (periodic) xx = wrap(xx, nx);
+                else if (xx < 0 || xx >= nx) continue;
+                red_add(acc + (int64_t)gy * nx + xx, vv[t]);
+            }
+        }
+    }
+}
+
+// ---- direct scatter (FP64 in 2D) ----------------------------------------
+template <typename UT, typename AT = typename UTraits<UT>::acc>
+__global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, AT scale,
                                                        const short4 *__restrict__ offs,
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
-                                                       const UT *__restrict__ u,
-                                                       typename UTraits<UT>::acc *__restrict__ Au) {
-    using AT = typename UTraits<UT>::acc;
+                                                       const UT *__restrict__ u, AT *__restrict__ Au) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= nx) return;
@@ -61,7 +158,8 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc,
     AT acc = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        if (w[k] == (AT)0) continue;
+        const AT wk = scale * w[k];
+        if (wk == (AT)0) continue;
 #pragma unroll
         for (int s = -1; s <= 1; s += 2) {
             int xn = x + s * ex[k], yn = y + s * ey[k];
@@ -72,21 +170,19 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc,
                 continue;
             }
             const int64_t zn = (int64_t)yn * nx + xn;
-            const AT flux = w[k] * (uz - to_acc(u[zn]));
+            const AT flux = wk * (uz - to_acc(u[zn]));
             acc += flux;
-            atomicAdd(Au + zn, -flux);
+            red_add(Au + zn, -flux);
         }
     }
-    atomicAdd(Au + z, acc);
+    red_add(Au + z, acc);
 }
 
-template <typename UT>
-__global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, int bc,
+template <typename UT, typename AT = typename UTraits<UT>::acc>
+__global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, int bc, AT scale,
                                                        const char4 *__restrict__ offs,
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
-                                                       const UT *__restrict__ u,
-                                                       typename UTraits<UT>::acc *__restrict__ Au) {
-    using AT = typename UTraits<UT>::acc;
+                                                       const UT *__restrict__ u, AT *__restrict__ Au) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, zc = blockIdx.z;
     if (x >= nx) return;
@@ -100,7 +196,8 @@ __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, i
     AT acc = 0;
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        if (w[q] == (AT)0) continue;
+        const AT wq = scale * w[q];
+        if (wq == (AT)0) continue;
 #pragma unroll
         for (int s = -1; s <= 1; s += 2) {
             int xn = x + s * c[q][0], yn = y + s * c[q][1], zn = zc + s * c[q][2];
@@ -112,24 +209,32 @@ __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, i
                 continue;
             }
             const int64_t zz = ((int64_t)zn * ny + yn) * nx + xn;
-            const AT flux = w[q] * (uz - to_acc(u[zz]));
+            const AT flux = wq * (uz - to_acc(u[zz]));
             acc += flux;
-            atomicAdd(Au + zz, -flux);
+            red_add(Au + zz, -flux);
         }
     }
-    atomicAdd(Au + z, acc);
+    red_add(Au + z, acc);
 }
 
-// u <- u - dt * acc ; acc <- 0
+// u <- u - acc ; acc <- 0   (acc already holds dt A u)
 template <typename UT>
-__global__ void axpy_zero_kernel(int64_t N, UT *__restrict__ u,
-                                 typename UTraits<UT>::acc *__restrict__ acc, double dt) {
+__global__ void finalize_kernel(int64_t N, UT *__restrict__ u,
+                                typename UTraits<UT>::acc *__restrict__ acc) {
     using AT = typename UTraits<UT>::acc;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     AT a = acc[i];
     acc[i] = (AT)0;
-    u[i] = from_acc<UT>(to_acc(u[i]) - (AT)dt * a);
+    u[i] = from_acc<UT>(to_acc(u[i]) - a);
+}
+
+__global__ void finalize_f32x4_kernel(int64_t N4, float4 *__restrict__ u, float4 *__restrict__ acc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N4) return;
+    float4 a = acc[i], v = u[i];
+    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    u[i] = make_float4(v.x - a.x, v.y - a.y, v.z - a.z, v.w - a.w);
 }
 
 // ---- canonical export --------------------------------------------------
@@ -161,7 +266,6 @@ __device__ __forceinline__ void write_canonical(int (&v)[K][DIM], double (&w)[K]
             for (int t = 0; t < DIM; ++t) v[k][t] = -v[k][t];
         }
     }
-    // insertion sort (K <= 6)
     int idx[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) idx[k] = k;
@@ -226,22 +330,60 @@ adlbr_status launch_export(const adlbr_stencils *s, int16_t *offs, void *w, cuda
     return ADLBR_OK;
 }
 
+// acc += scale * A u   (acc must hold zero or a partial sum on entry)
 template <typename UT>
-static adlbr_status apply_t(const adlbr_stencils *s, const UT *u, typename UTraits<UT>::acc *Au,
-                            cudaStream_t st) {
+static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename UTraits<UT>::acc *acc,
+                                 double scale, const int *skip, cudaStream_t st) {
     using AT = typename UTraits<UT>::acc;
-    ADLBR_CUDA(cudaMemsetAsync(Au, 0, (size_t)s->N * sizeof(AT), st));
     if (s->dim == 2) {
-        const int threads = 256;
-        dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
-        apply2d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc,
-                                                      (const short4 *)s->offs, s->w, s->w_t, u, Au);
+        if constexpr (sizeof(AT) == 4) {
+            dim3 grid(blocks_for(s->n[0], TW), blocks_for(s->n[1], TH));
+            apply2d_tiled<UT><<<grid, TILE_THREADS, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc,
+                                                             (float)scale, (const short4 *)s->offs,
+                                                             s->w, s->w_t, u, acc, skip);
+        } else {
+            const int threads = 256;
+            dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
+            apply2d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (AT)scale,
+                                                          (const short4 *)s->offs, s->w, s->w_t, u,
+                                                          acc);
+        }
     } else {
         const int threads = 128;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);
         apply3d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], (int)s->n[2],
-                                                      s->bc, (const char4 *)s->offs, s->w, s->w_t,
-                                                      u, Au);
+                                                      s->bc, (AT)scale, (const char4 *)s->offs, s->w,
+                                                      s->w_t, u, acc);
+    }
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,
+                               double scale, const int *skip, cudaStream_t st) {
+    switch (u_t) {
+    case ADLBR_F64: return accumulate_t<double>(s, (const double *)u, (double *)acc, scale, skip, st);
+    case ADLBR_F32: return accumulate_t<float>(s, (const float *)u, (float *)acc, scale, skip, st);
+    case ADLBR_F16: return accumulate_t<__half>(s, (const __half *)u, (float *)acc, scale, skip, st);
+    case ADLBR_BF16:
+        return accumulate_t<__nv_bfloat16>(s, (const __nv_bfloat16 *)u, (float *)acc, scale, skip, st);
+    }
+    return fail(ADLBR_E_ARG, "bad u dtype %d", (int)u_t);
+}
+
+adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, double *acc, double scale,
+                                   cudaStream_t st) {
+    if (s->dim == 2) {
+        const int threads = 256;
+        dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
+        apply2d_scatter<float, double><<<grid, threads, 0, st>>>(
+            (int)s->n[0], (int)s->n[1], s->bc, scale, (const short4 *)s->offs, s->w, s->w_t, u, acc);
+    } else {
+        const int threads = 128;
+        dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);
+        apply3d_scatter<float, double><<<grid, threads, 0, st>>>(
+            (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, scale, (const char4 *)s->offs, s->w,
+            s->w_t, u, acc);
     }
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
@@ -249,32 +391,32 @@ static adlbr_status apply_t(const adlbr_stencils *s, const UT *u, typename UTrai
 
 adlbr_status launch_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                           cudaStream_t st) {
-    switch (u_t) {
-    case ADLBR_F64: return apply_t<double>(s, (const double *)u, (double *)Au, st);
-    case ADLBR_F32: return apply_t<float>(s, (const float *)u, (float *)Au, st);
-    case ADLBR_F16: return apply_t<__half>(s, (const __half *)u, (float *)Au, st);
-    case ADLBR_BF16: return apply_t<__nv_bfloat16>(s, (const __nv_bfloat16 *)u, (float *)Au, st);
-    }
-    return fail(ADLBR_E_ARG, "bad u dtype %d", (int)u_t);
+    const size_t es = u_t == ADLBR_F64 ? sizeof(double) : sizeof(float);
+    ADLBR_CUDA(cudaMemsetAsync(Au, 0, (size_t)s->N * es, st));
+    return launch_accumulate(s, u, Au, u_t, 1.0, nullptr, st);
 }
 
-adlbr_status launch_axpy_zero(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
-                              double dt, cudaStream_t st) {
+adlbr_status launch_finalize(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
+                             cudaStream_t st) {
     const int threads = 256;
     unsigned blocks = blocks_for(s->N, threads);
     switch (u_t) {
     case ADLBR_F64:
-        axpy_zero_kernel<double><<<blocks, threads, 0, st>>>(s->N, (double *)u, (double *)acc, dt);
+        finalize_kernel<double><<<blocks, threads, 0, st>>>(s->N, (double *)u, (double *)acc);
         break;
     case ADLBR_F32:
-        axpy_zero_kernel<float><<<blocks, threads, 0, st>>>(s->N, (float *)u, (float *)acc, dt);
+        if (s->N % 4 == 0 && ((uintptr_t)u % 16) == 0 && ((uintptr_t)acc % 16) == 0)
+            finalize_f32x4_kernel<<<blocks_for(s->N / 4, threads), threads, 0, st>>>(
+                s->N / 4, (float4 *)u, (float4 *)acc);
+        else
+            finalize_kernel<float><<<blocks, threads, 0, st>>>(s->N, (float *)u, (float *)acc);
         break;
     case ADLBR_F16:
-        axpy_zero_kernel<__half><<<blocks, threads, 0, st>>>(s->N, (__half *)u, (float *)acc, dt);
+        finalize_kernel<__half><<<blocks, threads, 0, st>>>(s->N, (__half *)u, (float *)acc);
         break;
     case ADLBR_BF16:
-        axpy_zero_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(s->N, (__nv_bfloat16 *)u,
-                                                                    (float *)acc, dt);
+        finalize_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(s->N, (__nv_bfloat16 *)u,
+                                                                   (float *)acc);
         break;
     default: return fail(ADLBR_E_ARG, "bad u dtype %d", (int)u_t);
     }

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     T D[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) D[k] = Dp[(int64_t)k * N + i];
-    double wz[6] = {0, 0, 0, 0, 0, 0};
+    using WV = typename WVal<T>::type;
+    WV wz[6] = {};
 
     int code = 0;
 #pragma unroll
@@ -110,10 +111,10 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     }
 
     // ---- approximate greedy reduction (FP32) ----
-    const double scl = 1.0 / fmax((double)D[0], fmax((double)D[1], (double)D[2]));
+    const T dmax = D[0] > D[1] ? (D[0] > D[2] ? D[0] : D[2]) : (D[1] > D[2] ? D[1] : D[2]);
     float d[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) d[k] = (float)((double)D[k] * scl);
+    for (int k = 0; k < 6; ++k) d[k] = (float)(D[k] / dmax);
     V3 b[3] = {V3{1, 0, 0}, V3{0, 1, 0}, V3{0, 0, 1}};
     for (int it = 0; it < 24; ++it) {
         // sort by norm
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     constexpr int PK[6] = {2, 1, 1, 0, 0, 0};
     constexpr int PL[6] = {3, 3, 2, 3, 2, 1};
     int sg[6];
+    WV val[6];
     bool ok = false, range = false;
     for (int fix = 0; fix < 256; ++fix) {
         range = false;
@@ -207,7 +209,10 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
         int bad = -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            sg[q] = sgnD(D, e[PI[q]], e[PJ[q]]);
+            T x[6];
+            int n[6];
+            terms3(D, e[PI[q]], e[PJ[q]], x, n);
+            sg[q] = sign_value<6>(x, n, val[q]);
             if (sg[q] > 0 && bad < 0) bad = q;
         }
         if (bad < 0) {
@@ -233,10 +238,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
         if (sg[q] == 0) {
             zmask |= 1u << q;
         } else {
-            T x[6];
-            int n[6];
-            terms3(D, e[PI[q]], e[PJ[q]], x, n);
-            wz[q] = fmax(-0.5 * accurate_value<6>(x, n), 0.0);
+            wz[q] = wmax0(neg_half(val[q]));
         }
     }
 #pragma unroll

@@ -1,0 +1,274 @@
+// Implicit step (I + dt A) x = b by conjugate gradients (Sec. 4.2: the
+// discretised Eq. elliptic is solved by Conjugate Gradient; here with
+// lambda = dt and b = u^n).
+//
+// Vectors are FP32; every dot product and norm is accumulated in FP64 with a
+// deterministic two-level reduction (warp shuffles, one partial per block, and
+// the last block to finish sums the partials in block order).  The CG scalars
+// alpha, beta and |r|^2 live in device memory and are produced by that last
+// block, so an iteration needs no host round trip; the host polls a
+// convergence flag every few iterations.  Once the flag is set every kernel
+// returns immediately, so the reported iteration count is exact.
+//
+// Per iteration: q <- dt A p (operator accumulated into a zeroed q), then
+//   K2  q <- q + p ; <p, q> ; last block: alpha = rr / <p,q>
+//   K3  x += alpha p ; r -= alpha q ; q <- 0 ; <r, r> ; last block: beta, flag
+//   K4  p <- r + beta p
+#include <cmath>
+#include <cstddef>
+
+#include "internal.cuh"
+
+namespace adlbr {
+
+namespace {
+
+constexpr int RT = 256;   // threads per reduction block
+constexpr int RB = 1216;  // blocks of the vector kernels (8 per SM on 152 SMs)
+
+struct CgState {
+    double rr, rr_new, pq, alpha, beta, bb, tol2;
+    int conv, iters, max_iters;  // conv: 0 running, 1 converged, 2 iteration limit
+    unsigned int count;          // last-block ticket
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double warp_part[RT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_part[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < RT / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+// Writes this block's partial; returns true in thread 0 of the last block,
+// after which total = sum of all partials in block order.
+__device__ __forceinline__ bool finish_reduction(double part, double *partials, unsigned int *count,
+                                                 double &total) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = part;
+        __threadfence();
+        unsigned int t = atomicAdd(count, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) s += ((volatile double *)partials)[b];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        total = s;
+        *count = 0;
+    }
+    return threadIdx.x == 0;
+}
+
+// q <- q + p ; alpha = rr / <p, q>
+__global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__ p,
+                                            float *__restrict__ q, double *partials, CgState *S) {
+    if (S->conv) return;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        float qi = q[i] + p[i];
+        q[i] = qi;
+        s += (double)p[i] * qi;
+    }
+    double part = block_sum(s);
+    double tot;
+    if (finish_reduction(part, partials, &S->count, tot)) {
+        S->pq = tot;
+        S->alpha = S->rr / tot;
+    }
+}
+
+// x += alpha p ; r -= alpha q ; q <- 0 ; rr_new = <r, r> ; beta ; flag
+__global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, const float *__restrict__ p,
+                                            float *__restrict__ r, float *__restrict__ q,
+                                            double *partials, CgState *S) {
+    if (S->conv) return;
+    const float alpha = (float)S->alpha;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        x[i] += alpha * p[i];
+        float ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        q[i] = 0.f;
+        s += (double)ri * ri;
+    }
+    double part = block_sum(s);
+    double tot;
+    if (finish_reduction(part, partials, &S->count, tot)) {
+        S->beta = tot / S->rr;
+        S->rr = tot;
+        S->iters += 1;
+        if (tot <= S->tol2 * S->bb || !(tot == tot))
+            S->conv = 1;
+        else if (S->iters >= S->max_iters)
+            S->conv = 2;
+    }
+}
+
+// p <- r + beta p
+__global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r,
+                                            float *__restrict__ p, const CgState *S) {
+    if (S->conv) return;
+    const float beta = (float)S->beta;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
+        p[i] = r[i] + beta * p[i];
+}
+
+// (Re)start from the true residual: r = b - (x + dt A x) evaluated in FP64
+// (acc holds dt A x accumulated in FP64), rounded once to FP32; p = r.
+// rr_new = |r|^2 of the FP64 residual, rr = |r|^2 of its FP32 copy, bb = |b|^2;
+// conv = 1 when the true residual already meets the tolerance.
+__global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *__restrict__ b,
+                                                        const float *__restrict__ x,
+                                                        const double *__restrict__ acc,
+                                                        float *__restrict__ r, float *__restrict__ p,
+                                                        double *partials, double *partials2,
+                                                        double *partials3, CgState *S) {
+    double s_true = 0.0, s_rr = 0.0, s_bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const double bi = b[i];
+        const double ri = bi - ((double)x[i] + acc[i]);
+        const float rf = (float)ri;
+        r[i] = rf;
+        p[i] = rf;
+        s_true += ri * ri;
+        s_rr += (double)rf * rf;
+        s_bb += bi * bi;
+    }
+    const double pt = block_sum(s_true);
+    const double pr = block_sum(s_rr);
+    const double pb = block_sum(s_bb);
+    if (threadIdx.x == 0) {
+        partials2[blockIdx.x] = pr;
+        partials3[blockIdx.x] = pb;
+    }
+    double tot;
+    if (finish_reduction(pt, partials, &S->count, tot)) {
+        double rr = 0.0, bb = 0.0;
+        for (int k = 0; k < (int)gridDim.x; ++k) {
+            rr += ((volatile double *)partials2)[k];
+            bb += ((volatile double *)partials3)[k];
+        }
+        S->rr_new = tot;
+        S->rr = rr;
+        S->bb = bb;
+        S->iters = 0;
+        S->conv = (tot <= S->tol2 * bb) ? 1 : 0;
+    }
+}
+
+}  // namespace
+
+struct CgWorkspace {
+    float *r, *p, *q, *z;
+    double *acc64;  // aliases q and z (8 bytes per point), used between iterations
+    double *partials, *partials2, *partials3;
+    CgState *S;
+};
+
+static size_t cg_ws_bytes(int64_t N) {
+    return 4 * (size_t)N * sizeof(float) + 3 * RB * sizeof(double) + 256 + sizeof(CgState);
+}
+
+static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
+    size_t need = cg_ws_bytes(s->N);
+    if (!s->ws || s->ws_bytes < need) {
+        if (s->ws) cudaFree(s->ws);
+        s->ws = nullptr;
+        ADLBR_CUDA(cudaMalloc(&s->ws, need));
+        s->ws_bytes = need;
+    }
+    char *b = (char *)s->ws;
+    W.r = (float *)b;
+    W.p = W.r + s->N;
+    W.q = W.p + s->N;
+    W.z = W.q + s->N;
+    W.acc64 = (double *)W.q;
+    W.partials = (double *)(W.z + s->N);
+    W.partials2 = W.partials + RB;
+    W.partials3 = W.partials2 + RB;
+    uintptr_t a = (uintptr_t)(W.partials3 + RB);
+    a = (a + 255) & ~(uintptr_t)255;
+    W.S = (CgState *)a;
+    return ADLBR_OK;
+}
+
+static const int *conv_flag(const CgState *S) {
+    return (const int *)((const char *)S + offsetof(CgState, conv));
+}
+
+// CG on FP32 vectors with FP64 reductions, wrapped in iterative refinement:
+// every (re)start measures the true residual b - (I + dt A) x with the
+// operator accumulated in FP64, stops if it meets rtol, and otherwise runs CG
+// on the FP32-rounded residual until the recursive residual meets rtol.
+adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                    int *iters_out, double *relres_out, cudaStream_t st) {
+    CgWorkspace W;
+    if (adlbr_status e = cg_workspace(s, W)) return e;
+    const int64_t N = s->N;
+    CgState init = {};
+    init.tol2 = rtol * rtol;
+    CgState host = {};
+    int total_iters = 0;
+    double relres = INFINITY, prev = INFINITY;
+    bool cg_converged = false;
+    const int kMaxRestarts = 3;
+    for (int restart = 0; restart <= kMaxRestarts; ++restart) {
+        init.max_iters = maxit - total_iters;
+        ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
+        ADLBR_CUDA(cudaMemsetAsync(W.acc64, 0, N * sizeof(double), st));
+        if (adlbr_status e = launch_accumulate_f64(s, x, W.acc64, dt, st)) return e;
+        cg_restart_kernel<<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.r, W.p, W.partials, W.partials2,
+                                             W.partials3, W.S);
+        ADLBR_CUDA(cudaGetLastError());
+        ADLBR_CUDA(cudaMemsetAsync(W.q, 0, N * sizeof(float), st));  // q aliases acc64
+        ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        ADLBR_CUDA(cudaStreamSynchronize(st));
+        relres = host.bb > 0 ? std::sqrt(host.rr_new / host.bb) : 0.0;
+        // stop when the true residual meets rtol, when refinement stopped
+        // paying (x is FP32: the true residual floors near eps32 |I + dt A|),
+        // or when the budget is spent
+        if (relres <= rtol || total_iters >= maxit || restart == kMaxRestarts) break;
+        if (restart > 0 && !(relres < 0.5 * prev)) break;
+        prev = relres;
+        const int chunk = 8;
+        int it = 0;
+        while (it < maxit - total_iters) {
+            for (int k = 0; k < chunk; ++k) {
+                if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), st))
+                    return e;
+                cg_k2<<<RB, RT, 0, st>>>(N, W.p, W.q, W.partials, W.S);
+                cg_k3<<<RB, RT, 0, st>>>(N, x, W.p, W.r, W.q, W.partials, W.S);
+                cg_k4<<<RB, RT, 0, st>>>(N, W.r, W.p, W.S);
+            }
+            ADLBR_CUDA(cudaGetLastError());
+            it += chunk;
+            ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            ADLBR_CUDA(cudaStreamSynchronize(st));
+            if (host.conv) break;
+        }
+        total_iters += host.iters;
+        cg_converged = host.conv == 1;
+    }
+    if (iters_out) *iters_out = total_iters;
+    if (relres_out) *relres_out = relres;
+    if (!(relres <= rtol) && !cg_converged)
+        return fail(ADLBR_E_NOT_CONVERGED, "CG stopped at relative residual %.3e after %d iterations",
+                    relres, total_iters);
+    return ADLBR_OK;
+}
+
+}  // namespace adlbr

@@ -18,6 +18,18 @@
 
 namespace adlbr {
 
+// An unevaluated float-float sum hi + lo (weights computed from FP32 tensors;
+// no FP64 instruction on that path: GB300's FP64 rate is a small fraction of
+// its FP32 rate).
+struct FF {
+    float hi, lo;
+};
+
+// Value type of the accurately evaluated weights for input element type T.
+template <typename T> struct WVal;
+template <> struct WVal<float> { using type = FF; };
+template <> struct WVal<double> { using type = double; };
+
 __device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
     s = __dadd_rn(a, b);
     double bv = __dsub_rn(s, a);
@@ -132,6 +144,57 @@ __device__ __forceinline__ double accurate_value_f64(const double (&x)[K], const
     return __dadd_rn(s, c);
 }
 
+// Exact sign and accurate value together.  The float-float accumulation has
+// forward error below 4 K^2 u^2 sum|n_k x_k| (u = 2^-24): every product is
+// split exactly, the running sum is kept with TwoSum, and only the small
+// correction term is rounded.  With a factor-2 margin this is a filter some
+// 10^6 times tighter than plain FP32 evaluation, so the exact expansion runs
+// only for true ties (or differences below ~1e-13 of the terms).
+template <int K>
+__device__ __forceinline__ int sign_value(const float (&x)[K], const int (&n)[K], FF &val) {
+    float s = 0.f, c = 0.f, A = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float nk = (float)n[k];
+        const float p = __fmul_rn(nk, x[k]);
+        const float pe = __fmaf_rn(nk, x[k], -p);
+        const float t = __fadd_rn(s, p);
+        const float bv = __fsub_rn(t, s);
+        const float av = __fsub_rn(t, bv);
+        const float err = __fadd_rn(__fsub_rn(s, av), __fsub_rn(p, bv));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, pe));
+        A = __fadd_rn(A, fabsf(p));
+    }
+    val = FF{s, c};
+    if (A == 0.f) return 0;
+    const float v = __fadd_rn(s, c);
+    const float bound = __fmaf_rn(A, (float)(8 * K * K) * 0x1p-48f, 0x1p-126f);
+    if (fabsf(v) > bound) return v > 0.f ? 1 : -1;
+    return exact_sign_slow_f32<K>(x, n);
+}
+
+template <int K>
+__device__ __forceinline__ int sign_value(const double (&x)[K], const int (&n)[K], double &val) {
+    double s = 0.0, c = 0.0, A = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double nk = (double)n[k];
+        const double p = __dmul_rn(nk, x[k]);
+        const double pe = __fma_rn(nk, x[k], -p);
+        double t, err;
+        two_sum_d(s, p, t, err);
+        s = t;
+        c = __dadd_rn(c, __dadd_rn(err, pe));
+        A = __dadd_rn(A, fabs(p));
+    }
+    val = __dadd_rn(s, c);
+    if (A == 0.0) return 0;
+    const double bound = __fma_rn(A, (double)(8 * K * K) * 0x1p-106, 0x1p-1000);
+    if (fabs(val) > bound) return val > 0.0 ? 1 : -1;
+    return exact_sign_slow_f64<K>(x, n);
+}
+
 // Dispatch on the input type.
 template <int K>
 __device__ __forceinline__ int exact_sign(const float (&x)[K], const int (&n)[K]) {
@@ -142,8 +205,8 @@ __device__ __forceinline__ int exact_sign(const double (&x)[K], const int (&n)[K
     return exact_sign_f64<K>(x, n);
 }
 template <int K>
-__device__ __forceinline__ double accurate_value(const float (&x)[K], const int (&n)[K]) {
-    // float-float accumulation, returned as its (double) sum
+__device__ __forceinline__ FF accurate_value(const float (&x)[K], const int (&n)[K]) {
+    // float-float accumulation of the exact products, returned unevaluated
     float s = 0.f, c = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -157,7 +220,7 @@ __device__ __forceinline__ double accurate_value(const float (&x)[K], const int 
         s = t;
         c = __fadd_rn(c, __fadd_rn(err, pe));
     }
-    return __dadd_rn((double)s, (double)c);
+    return FF{s, c};
 }
 template <int K>
 __device__ __forceinline__ double accurate_value(const double (&x)[K], const int (&n)[K]) {

@@ -74,17 +74,46 @@ template <> struct UTraits<float> { using acc = float; };
 template <> struct UTraits<__half> { using acc = float; };
 template <> struct UTraits<__nv_bfloat16> { using acc = float; };
 
+// FP16 / BF16 <-> FP32 conversions in integer and FP32 arithmetic.  On GB300
+// the hardware conversion instructions issue to the narrow FP64 pipe (ncu
+// shows it busy in a kernel whose only non-FP32 work is half -> float), so the
+// hot paths convert with bit operations instead.
+__device__ __forceinline__ float h2f_bits(uint16_t h) {
+    const uint32_t mag = (uint32_t)(h & 0x7fffu) << 13;  // exponent, mantissa in FP32 position
+    float f = __fmul_rn(__uint_as_float(mag), 0x1p112f);  // rebias 15 -> 127 (subnormals too)
+    if ((h & 0x7c00u) == 0x7c00u) f = __uint_as_float(0x7f800000u | mag);  // inf / nan
+    return __uint_as_float(__float_as_uint(f) | ((uint32_t)(h & 0x8000u) << 16));
+}
+// Round to nearest even; finite inputs beyond the FP16 range give infinity.
+__device__ __forceinline__ uint16_t f2h_bits(float f) {
+    const uint32_t x = __float_as_uint(f);
+    const uint32_t sign = (x >> 16) & 0x8000u;
+    const float a = fabsf(f);
+    if (!(a < 65520.f)) return (uint16_t)(sign | (a != a ? 0x7e00u : 0x7c00u));
+    const uint32_t b = __float_as_uint(__fmul_rn(a, 0x1p-112f));  // exponent rebias 127 -> 15
+    const uint32_t r = (b + 0x0fffu + ((b >> 13) & 1u)) >> 13;
+    return (uint16_t)(sign | r);
+}
+__device__ __forceinline__ float bf2f_bits(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+__device__ __forceinline__ uint16_t f2bf_bits(float f) {
+    const uint32_t x = __float_as_uint(f);
+    if ((x & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((x >> 16) | 0x40u);  // nan
+    return (uint16_t)((x + 0x7fffu + ((x >> 16) & 1u)) >> 16);
+}
+
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
-__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
-__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(__half v) { return h2f_bits(__half_as_ushort(v)); }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return bf2f_bits(__bfloat16_as_ushort(v)); }
 
 template <typename T> __device__ __forceinline__ T from_acc(typename UTraits<T>::acc v);
 template <> __device__ __forceinline__ double from_acc<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_acc<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half from_acc<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half from_acc<__half>(float v) {
+    return __ushort_as_half(f2h_bits(v));
+}
 template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) {
-    return __float2bfloat16_rn(v);
+    return __ushort_as_bfloat16(f2bf_bits(v));
 }
 
 // ---------------------------------------------------------------- weights
@@ -103,7 +132,7 @@ __device__ __forceinline__ unsigned load_weights(const void *wbase, adlbr_dtype 
             int s = (int)(int8_t)(meta >> 8);
             float sc = __int_as_float((127 + s) << 23);
 #pragma unroll
-            for (int k = 0; k < K; ++k) w[k] = (Acc)(__half2float(h[k]) * sc);
+            for (int k = 0; k < K; ++k) w[k] = (Acc)(h2f_bits(__half_as_ushort(h[k])) * sc);
             return meta & 0xffu;
         } else {
             uint4 r = p[i];
@@ -113,7 +142,7 @@ __device__ __forceinline__ unsigned load_weights(const void *wbase, adlbr_dtype 
             int s = (int)(int8_t)(meta >> 8);
             float sc = __int_as_float((127 + s) << 23);
 #pragma unroll
-            for (int k = 0; k < K; ++k) w[k] = (Acc)(__half2float(h[k]) * sc);
+            for (int k = 0; k < K; ++k) w[k] = (Acc)(h2f_bits(__half_as_ushort(h[k])) * sc);
             return meta & 0xffu;
         }
     } else if (wt == ADLBR_F32) {
@@ -154,7 +183,25 @@ adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, c
 adlbr_status launch_export(const adlbr_stencils *s, int16_t *offs, void *w, cudaStream_t st);
 adlbr_status launch_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                           cudaStream_t st);
-adlbr_status launch_axpy_zero(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
-                              double dt, cudaStream_t st);
+size_t ced_tensor_scratch_bytes(int64_t N);
+adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double sigma, double rho,
+                               double alpha, double C, void *scratch, cudaStream_t st);
+// CED tensor stage fused with the 2D stencil construction into handle s
+// (Dtmp, 3N floats, is only used by the fallback path for unusual radii).
+adlbr_status launch_ced_build(adlbr_stencils *s, const float *u, double sigma, double rho,
+                              double alpha, double C, void *scratch, float *Dtmp, cudaStream_t st);
+adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                    int *iters_out, double *relres_out, cudaStream_t st);
+// acc += scale * A u (accumulation type: double for F64 u, float otherwise);
+// a kernel launched with skip != NULL returns at once when *skip != 0.
+adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,
+                               double scale, const int *skip, cudaStream_t st);
+// acc (double) += scale * A u for FP32 u: the FP64-accumulated operator used to
+// measure true residuals.
+adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, double *acc, double scale,
+                                   cudaStream_t st);
+// u <- u - acc ; acc <- 0
+adlbr_status launch_finalize(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
+                             cudaStream_t st);
 
 }  // namespace adlbr

@@ -1,0 +1,206 @@
+// The 2D AD-LBR stencil of one grid point (device function shared by the
+// stand-alone build kernel and the fused CED tensor + build kernel).
+//
+// Sec. 2 of the paper: (i) an M(z)-reduced basis (e, f) by Lagrange's
+// algorithm (Eq. GaussAlgo), (ii) f negated if <e, M f> > 0, (iii) the
+// M-obtuse superbase (e, f, -e-f) (Corollary
+// ObtuseSuperBaseFromReducedBasis2), stencil Eq. def:Vz and weights
+// Eq. def:GammaZ.  M is a positive multiple of S = adj(D) (Eqs. def:M,
+// eq:DM), and <e^perp, D f^perp> = <e, S f>.
+//
+// GPU design: the reduction loop runs in FP32 on a rescaled S (cheap, a few
+// iterations); its output is then CERTIFIED: the three products
+// <e_i, S e_j> of the superbase are signed exactly (exact.cuh) against the
+// input D, and while one of them is positive a Selling step
+// (e_i, e_j, e_k) -> (-e_i, e_j, e_i - e_j) (which lowers sum |e|_S^2 by
+// 4 <e_i, S e_j>) repairs it.  The result is an exactly S-obtuse superbase;
+// by Lemma indepBasis its positive-weight stencil is unique, so the offsets
+// agree bit for bit with any other exact construction.
+#pragma once
+
+#include "exact.cuh"
+#include "internal.cuh"
+#include "store.cuh"
+
+namespace adlbr {
+namespace s2d {
+
+struct V2 {
+    int x, y;
+};
+
+__device__ __forceinline__ float gram2(float sxx, float sxy, float syy, V2 u, V2 v) {
+    float ux = (float)u.x, uy = (float)u.y, vx = (float)v.x, vy = (float)v.y;
+    return sxx * ux * vx + sxy * (ux * vy + uy * vx) + syy * uy * vy;
+}
+
+// <u, adj(D) v> = c ux vx - b (ux vy + uy vx) + a uy vy, terms (x_k, n_k).
+template <typename T>
+__device__ __forceinline__ void terms2(T a, T b, T c, V2 u, V2 v, T (&x)[3], int (&n)[3]) {
+    x[0] = c;
+    n[0] = u.x * v.x;
+    x[1] = b;
+    n[1] = -(u.x * v.y + u.y * v.x);
+    x[2] = a;
+    n[2] = u.y * v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ int sgnS(T a, T b, T c, V2 u, V2 v) {
+    T x[3];
+    int n[3];
+    terms2(a, b, c, u, v, x, n);
+    return exact_sign<3>(x, n);
+}
+
+static __device__ __noinline__ bool det_positive_slow(float a, float b, float c) {
+    // a c and b^2 are exact in FP64; the rounded difference keeps the sign
+    return __dsub_rn(__dmul_rn((double)a, (double)c), __dmul_rn((double)b, (double)b)) > 0.0;
+}
+__device__ __forceinline__ bool det_positive(float a, float b, float c) {
+    // a c - b^2 = (p1 + e1) - (p2 + e2) exactly (fma splits); FP32 filter first
+    const float p1 = __fmul_rn(a, c), e1 = __fmaf_rn(a, c, -p1);
+    const float p2 = __fmul_rn(b, b), e2 = __fmaf_rn(b, b, -p2);
+    const float v = __fadd_rn(__fsub_rn(p1, p2), __fsub_rn(e1, e2));
+    const float bound = __fmul_rn(__fadd_rn(fabsf(p1), fabsf(p2)), 0x1p-20f);
+    if (fabsf(v) > bound) return v > 0.f;
+    return det_positive_slow(a, b, c);
+}
+__device__ __forceinline__ bool det_positive(double a, double b, double c) {
+    double p = __dmul_rn(a, c), pe = __fma_rn(a, c, -p);
+    double q = __dmul_rn(-b, b), qe = __fma_rn(-b, b, -q);
+    double h[5];
+    int m = 0;
+    m = grow_expansion(h, m, pe);
+    m = grow_expansion(h, m, p);
+    m = grow_expansion(h, m, qe);
+    m = grow_expansion(h, m, q);
+    return m > 0 && h[m - 1] > 0.0;
+}
+
+__device__ __forceinline__ bool finite(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// S = adj(D) / max(a, c) in FP32, for the approximate reduction loop.
+__device__ __forceinline__ void scaled_adj(float a, float b, float c, float &sxx, float &sxy,
+                                           float &syy) {
+    const float m = fmaxf(a, c);
+    sxx = c / m;
+    sxy = -b / m;
+    syy = a / m;
+}
+__device__ __forceinline__ void scaled_adj(double a, double b, double c, float &sxx, float &sxy,
+                                           float &syy) {
+    const double m = fmax(a, c);
+    sxx = (float)(c / m);
+    sxy = (float)(-b / m);
+    syy = (float)(a / m);
+}
+
+constexpr int kMaxReduce = 64;
+constexpr int kMaxFix = 256;
+// |coordinates| <= 2047 keeps every integer of the predicates below 2^24
+constexpr int kMaxCoord = 2047;
+
+}  // namespace s2d
+
+// Builds and stores the stencil of point i from D = [[a, b], [b, c]].
+template <typename T>
+__device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
+                                              void *wbase, adlbr_dtype wt, int *err) {
+    using namespace s2d;
+    using WV = typename WVal<T>::type;
+    WV wz[3] = {};
+    int code = 0;
+    if (!finite(a) || !finite(b) || !finite(c)) {
+        code = ERRBIT_NONFINITE;
+    } else if (!(a > (T)0) || !(c > (T)0) || !det_positive(a, b, c)) {
+        code = ERRBIT_NOT_SPD;
+    }
+    if (code) {
+        offs[i] = make_short4(0, 0, 0, 0);
+        store_weights<3>(wbase, wt, i, wz, 7u);
+        atomicOr(err, code);
+        return;
+    }
+
+    // (i) approximate Lagrange reduction in FP32 on S / max(a, c)
+    float sxx, sxy, syy;
+    scaled_adj(a, b, c, sxx, sxy, syy);
+    V2 e{1, 0}, f{0, 1};
+    for (int it = 0; it < kMaxReduce; ++it) {
+        float den = gram2(sxx, sxy, syy, f, f);
+        if (!(den > 0.f)) break;
+        float r = rintf(gram2(sxx, sxy, syy, e, f) / den);
+        r = fminf(fmaxf(r, -2048.f), 2048.f);
+        int q = (int)r;
+        V2 nf{e.x - q * f.x, e.y - q * f.y};
+        e = f;
+        f = nf;
+        if (abs(f.x) > kMaxCoord || abs(f.y) > kMaxCoord) break;
+        if (!(gram2(sxx, sxy, syy, e, e) > gram2(sxx, sxy, syy, f, f))) break;
+    }
+    // (ii) orientation of f
+    if (gram2(sxx, sxy, syy, e, f) > 0.f) f = V2{-f.x, -f.y};
+
+    // (iii) superbase, certified and repaired with exact signs
+    V2 v[3] = {e, f, V2{-e.x - f.x, -e.y - f.y}};
+    int sg[3];
+    WV val[3];
+    bool ok = false;
+    for (int fix = 0; fix < kMaxFix; ++fix) {
+        int bad = -1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T x[3];
+            int n[3];
+            terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
+            sg[k] = sign_value<3>(x, n, val[k]);
+            if (sg[k] > 0 && bad < 0) bad = k;
+        }
+        if (bad < 0) {
+            ok = true;
+            break;
+        }
+        // pair (j, l) = (bad+1, bad+2) is acute: (v_j, v_l, v_bad) -> (-v_j, v_l, v_j - v_l)
+        const int j = (bad + 1) % 3, l = (bad + 2) % 3;
+        V2 vj = v[j], vl = v[l];
+        v[j] = V2{-vj.x, -vj.y};
+        v[bad] = V2{vj.x - vl.x, vj.y - vl.y};
+        if (abs(v[bad].x) > kMaxCoord || abs(v[bad].y) > kMaxCoord) break;
+    }
+    bool range = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) range |= abs(v[k].x) > kMaxCoord || abs(v[k].y) > kMaxCoord;
+    if (!ok || range) {
+        offs[i] = make_short4(0, 0, 0, 0);
+        store_weights<3>(wbase, wt, i, wz, 7u);
+        atomicOr(err, range ? ERRBIT_RANGE : ERRBIT_NOT_CONVERGED);
+        return;
+    }
+
+    // weights gamma(+-e_k) = -<e_{k+1}, S e_{k+2}> / 2
+    unsigned zmask = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (sg[k] == 0) {
+            zmask |= 1u << k;
+            wz[k] = WV{};
+        } else {
+            wz[k] = wmax0(neg_half(val[k]));
+        }
+    }
+    offs[i] = make_short4((short)v[0].x, (short)v[0].y, (short)v[1].x, (short)v[1].y);
+    store_weights<3>(wbase, wt, i, wz, zmask);
+}
+
+// Out-of-line copy for kernels that reach the construction from inside large
+// unrolled bodies (one copy of its code instead of one per call site keeps
+// their instruction footprint small).
+static __device__ __noinline__ void build_point2d_call(float a, float b, float c, int64_t i,
+                                                       short4 *offs, void *wbase, adlbr_dtype wt,
+                                                       int *err) {
+    build_point2d<float>(a, b, c, i, offs, wbase, wt, err);
+}
+
+}  // namespace adlbr

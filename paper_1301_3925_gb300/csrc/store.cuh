@@ -1,32 +1,47 @@
 // Writing one point's weights in the handle's storage format.
 #pragma once
 
+#include "exact.cuh"
 #include "internal.cuh"
 
 namespace adlbr {
 
+__device__ __forceinline__ float to_f(FF v) { return __fadd_rn(v.hi, v.lo); }
+__device__ __forceinline__ double to_d(FF v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ float to_f(double v) { return (float)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ FF neg_half(FF v) { return FF{-0.5f * v.hi, -0.5f * v.lo}; }
+__device__ __forceinline__ double neg_half(double v) { return -0.5 * v; }
+__device__ __forceinline__ FF wmax0(FF v) { return (v.hi > 0.f || (v.hi == 0.f && v.lo > 0.f)) ? v : FF{0.f, 0.f}; }
+__device__ __forceinline__ double wmax0(double v) { return fmax(v, 0.0); }
+
 // w[0..K) are the weights (>= 0, +0 where zmask has the bit set).
-template <int K>
+template <int K, typename V>
 __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64_t i,
-                                              const double (&w)[K], unsigned zmask) {
+                                              const V (&w)[K], unsigned zmask) {
     constexpr int L = (K == 3) ? 4 : 8;
     if (wt == ADLBR_F16) {
-        double wmax = 0.0;
+        float wf[K];
+        float wmax = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) wmax = fmax(wmax, w[k]);
+        for (int k = 0; k < K; ++k) {
+            wf[k] = to_f(w[k]);
+            wmax = fmaxf(wmax, wf[k]);
+        }
         // per-point scale 2^s with wmax / 2^s in [1/2, 1): 11 significant
         // bits for the largest weight, no underflow for ratios above 2^-14
         int s = 0;
-        if (wmax > 0.0) {
-            s = ilogb(wmax) + 1;
+        if (wmax > 0.f) {
+            const int ex = (__float_as_int(wmax) >> 23) & 0xff;  // biased exponent
+            s = (ex == 0 ? -126 : ex - 127) + 1;
             s = max(-120, min(120, s));
         }
-        double inv = ldexp(1.0, -s);
+        const float inv = __int_as_float((127 - s) << 23);
         __half h[L];
 #pragma unroll
-        for (int k = 0; k < L; ++k) h[k] = __float2half_rn(0.f);
+        for (int k = 0; k < L; ++k) h[k] = __ushort_as_half((unsigned short)0);
 #pragma unroll
-        for (int k = 0; k < K; ++k) h[k] = __float2half_rn((float)(w[k] * inv));
+        for (int k = 0; k < K; ++k) h[k] = __ushort_as_half(f2h_bits(wf[k] * inv));
         uint16_t meta = (uint16_t)((zmask & 0xffu) | ((unsigned)(uint8_t)(int8_t)s << 8));
         *reinterpret_cast<uint16_t *>(&h[K]) = meta;
         if (L == 4)
@@ -38,7 +53,7 @@ __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64
 #pragma unroll
         for (int k = 0; k < L; ++k) v[k] = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = (float)w[k];
+        for (int k = 0; k < K; ++k) v[k] = to_f(w[k]);
         v[K] = (float)zmask;
         float *p = reinterpret_cast<float *>(wbase) + i * L;
 #pragma unroll
@@ -48,7 +63,7 @@ __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64
 #pragma unroll
         for (int k = 0; k < L; ++k) v[k] = 0.0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = w[k];
+        for (int k = 0; k < K; ++k) v[k] = to_d(w[k]);
         v[K] = (double)zmask;
         double *p = reinterpret_cast<double *>(wbase) + i * L;
 #pragma unroll

@@ -1,0 +1,57 @@
+"""Parity of the CUDA implicit step (CG on (I + dt A) x = b) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1301_3925_gb300 import adlbr as ab
+
+from gpu_helpers import build, dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("bc", [ab.NEUMANN, ab.PERIODIC])
+def test_cg_matches_oracle(bc):
+    t = torch()
+    shape = (96, 112)
+    D = synth.smooth_field2d(*shape, seed=3, kappa_min=1, kappa_max=50, lattice=8)
+    h, seen, _ = build(D, shape, t.float32, ab.F32, bc)
+    oo, ow, st, _ = oracle.build2d(*seen.reshape(3, -1))
+    dt = 200.0 * oracle.dt_limit(shape, bc, oo, ow)
+    b = synth.u_uniform(shape, 3)
+    try:
+        bd = dev(b.ravel(), t.float32)
+        x = bd.clone()
+        it, rel = ab.adlbr_step_implicit(h, bd, x, dt, 1e-6, 2000)
+        xg = x.double().cpu().numpy().reshape(shape)
+        bs = bd.double().cpu().numpy().reshape(shape)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    # true residual of the FP32 solution, by the oracle in FP64: x stored in
+    # FP32 bounds it near eps32 |I + dt A| (a few 1e-6 at dt = 200 dt_expl)
+    res = bs - (xg + dt * oracle.apply(shape, bc, oo, ow, xg))
+    true_rel = np.linalg.norm(res) / np.linalg.norm(bs)
+    assert true_rel <= 5e-6, true_rel
+    assert abs(rel - true_rel) <= 0.05 * true_rel + 1e-9   # the library reports it
+    xo, ito, relo = oracle.cg(shape, bc, oo, ow, bs, bs, dt, rtol=1e-10)
+    assert np.abs(xg - xo).max() <= 1e-4 * np.abs(xo).max()
+    # same Krylov method: the first CG round takes about the iterations of FP64
+    # CG at 1e-6; a refinement round from the true residual may add a few
+    _, ito6, _ = oracle.cg(shape, bc, oo, ow, bs, bs, dt, rtol=1e-6)
+    assert ito6 - 3 <= it <= ito6 + max(10, 0.15 * ito6), (it, ito6)
+
+
+def test_cg_iteration_limit_reports_not_converged():
+    t = torch()
+    shape = (64, 64)
+    D = synth.smooth_field2d(*shape, seed=4, kappa_min=1, kappa_max=50, lattice=8)
+    h, seen, _ = build(D, shape, t.float32, ab.F32)
+    try:
+        b = dev(synth.u_uniform(shape, 5).ravel(), t.float32)
+        x = b.clone()
+        with pytest.raises(ab.AdlbrError) as ei:
+            ab.adlbr_step_implicit(h, b, x, 500.0, 1e-8, 3)
+        assert ei.value.status == 5
+    finally:
+        ab.adlbr_stencils_destroy(h)
