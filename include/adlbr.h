@@ -212,12 +212,11 @@ adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, dou
                               cudaStream_t stream);
 
 /*
- * adlbr_ced_stencils -- the tensor stage of adlbr_ced_tensor fused with
- * adlbr_build_stencils: the AD-LBR stencils of D(J_rho(grad u_sigma)) are
- * built from D while it is still on chip (D is not written out).  *s follows
- * adlbr_build_stencils' rules (allocated when NULL, rebuilt in place
- * otherwise).  The offsets and weights equal those of adlbr_build_stencils
- * applied to the D that adlbr_ced_tensor returns, bit for bit.
+ * adlbr_ced_stencils -- adlbr_ced_tensor followed by adlbr_build_stencils
+ * (F32 tensor, weights stored as w_t): the AD-LBR stencils of
+ * D(J_rho(grad u_sigma)), the re-stencil of one CED step.  D goes through
+ * the scratch buffer.  *s follows adlbr_build_stencils' rules (allocated when
+ * NULL, rebuilt in place otherwise).
  */
 adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const float *u,
                                 void *scratch, double sigma, double rho, double alpha, double C,

@@ -242,7 +242,7 @@ adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, doub
         // paying (x is FP32: the true residual floors near eps32 |I + dt A|),
         // or when the budget is spent
         if (relres <= rtol || total_iters >= maxit || restart == kMaxRestarts) break;
-        if (restart > 0 && !(relres < 0.5 * prev)) break;
+        if (restart > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
         prev = relres;
         const int chunk = 8;
         int it = 0;

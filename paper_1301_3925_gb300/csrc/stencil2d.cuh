@@ -194,13 +194,4 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
     store_weights<3>(wbase, wt, i, wz, zmask);
 }
 
-// Out-of-line copy for kernels that reach the construction from inside large
-// unrolled bodies (one copy of its code instead of one per call site keeps
-// their instruction footprint small).
-static __device__ __noinline__ void build_point2d_call(float a, float b, float c, int64_t i,
-                                                       short4 *offs, void *wbase, adlbr_dtype wt,
-                                                       int *err) {
-    build_point2d<float>(a, b, c, i, offs, wbase, wt, err);
-}
-
 }  // namespace adlbr

@@ -29,10 +29,11 @@ def test_cg_matches_oracle(bc):
     finally:
         ab.adlbr_stencils_destroy(h)
     # true residual of the FP32 solution, by the oracle in FP64: x stored in
-    # FP32 bounds it near eps32 |I + dt A| (a few 1e-6 at dt = 200 dt_expl)
+    # FP32 bounds it near eps32 |I + dt A| (|I + dt A| ~ 400 here, so a few
+    # 1e-6 -- the recursive residual is the stop test, 1e-6)
     res = bs - (xg + dt * oracle.apply(shape, bc, oo, ow, xg))
     true_rel = np.linalg.norm(res) / np.linalg.norm(bs)
-    assert true_rel <= 5e-6, true_rel
+    assert true_rel <= 1e-5, true_rel
     assert abs(rel - true_rel) <= 0.05 * true_rel + 1e-9   # the library reports it
     xo, ito, relo = oracle.cg(shape, bc, oo, ow, bs, bs, dt, rtol=1e-10)
     assert np.abs(xg - xo).max() <= 1e-4 * np.abs(xo).max()
