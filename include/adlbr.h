@@ -157,6 +157,34 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
                                  double dt, int nsteps, cudaStream_t stream);
 
 /*
+ * adlbr_step_explicit_noalloc -- adlbr_step_explicit without any allocation.
+ *
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * allocate device memory while they step -- code inside a host application or
+ * framework that owns the device's whole memory pool, a real-time loop that
+ * must not call an allocator (cudaMalloc can block and synchronise the
+ * device), or a plugin that is not allowed to allocate at all.  It computes
+ * exactly what adlbr_step_explicit computes, but the scratch buffer (the
+ * accumulator of dt A u) is a fixed 16 MiB array inside this library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *  - Limit: at most 4,194,304 grid points for F32, F16 and BF16 u and
+ *    2,097,152 for F64 u; larger grids return ADLBR_E_SHAPE.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ *    first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it: make that first call before any
+ *    stream capture.
+ *  - All calls share the one array, which keeps the last call's contents
+ *    (each call clears the part it uses before using it).  Calls that may
+ *    overlap on the GPU -- on different streams, for different handles or
+ *    from different threads -- race on it and give wrong results: serialise
+ *    them.
+ *  - The current device must be the handle's device (else ADLBR_E_ARG).
+ */
+adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr_dtype u_t,
+                                         double dt, int nsteps, cudaStream_t stream);
+
+/*
  * adlbr_step_implicit -- one implicit step: solves (I + dt A) x = rhs by
  * conjugate gradients (the discretised Eq. elliptic of Sec. 4.2 with
  * lambda = dt, solved by CG as there).  FP32 vectors; every dot product and

@@ -63,6 +63,7 @@ def lib():
             "adlbr_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
             "adlbr_step_scratch_bytes": (ctypes.c_size_t, [_vp, _i32]),
             "adlbr_step_explicit": (_i32, [_vp, _vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
+            "adlbr_step_explicit_noalloc": (_i32, [_vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
             "adlbr_step_implicit": (_i32, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
@@ -157,6 +158,12 @@ def adlbr_step_scratch_bytes(h, u_t):
 def adlbr_step_explicit(h, u, scratch, u_t, dt, nsteps, stream=None):
     _check(lib().adlbr_step_explicit(h, _ptr(u), _ptr(scratch), u_t, float(dt), int(nsteps),
                                      _stream(stream)))
+
+
+def adlbr_step_explicit_noalloc(h, u, u_t, dt, nsteps, stream=None):
+    """The explicit step with the library's fixed scratch array (no allocation)."""
+    _check(lib().adlbr_step_explicit_noalloc(h, _ptr(u), u_t, float(dt), int(nsteps),
+                                             _stream(stream)))
 
 
 def adlbr_ced_scratch_bytes(g):

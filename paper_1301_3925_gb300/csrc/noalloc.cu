@@ -1,0 +1,75 @@
+// adlbr_step_explicit_noalloc: the explicit step with its scratch buffer in a
+// fixed device array of this library instead of caller- or library-allocated
+// memory (see include/adlbr.h for who needs it and its limits).
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace adlbr {
+
+namespace {
+
+// 16 MiB: the FP32 accumulator of up to 4,194,304 points, or the FP64 one of
+// up to 2,097,152 points.  Every GPU that loads the library holds it until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device; the host-side name is only a stand-in, never a device address).
+adlbr_status scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(ADLBR_E_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return ADLBR_OK;
+}
+
+size_t max_points(adlbr_dtype u_t) {
+    return kNoAllocScratchBytes / (u_t == ADLBR_F64 ? sizeof(double) : sizeof(float));
+}
+
+}  // namespace
+
+}  // namespace adlbr
+
+using namespace adlbr;
+
+extern "C" adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u,
+                                                    adlbr_dtype u_t, double dt, int nsteps,
+                                                    cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!u) return fail(ADLBR_E_ARG, "null buffer");
+    if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
+    if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
+    const size_t limit = max_points(u_t);
+    if ((size_t)s->N > limit)
+        return fail(ADLBR_E_SHAPE,
+                    "grid of %lld points exceeds the %zu-point limit of the allocation-free step "
+                    "(%zu MiB static scratch); use adlbr_step_explicit with caller scratch",
+                    (long long)s->N, limit, kNoAllocScratchBytes >> 20);
+    int dev = -1;
+    ADLBR_CUDA(cudaGetDevice(&dev));
+    if (dev != s->device)
+        return fail(ADLBR_E_ARG, "current device %d is not the handle's device %d", dev, s->device);
+    if (nsteps == 0) return ADLBR_OK;
+    void *acc = nullptr;
+    if (adlbr_status st = scratch_address(dev, &acc)) return st;
+    // the array keeps the previous call's contents: clear the accumulator
+    const size_t bytes = (size_t)s->N * (u_t == ADLBR_F64 ? sizeof(double) : sizeof(float));
+    ADLBR_CUDA(cudaMemsetAsync(acc, 0, bytes, stream));
+    for (int k = 0; k < nsteps; ++k) {
+        if (adlbr_status st = launch_accumulate(s, u, acc, u_t, dt, nullptr, stream)) return st;
+        if (adlbr_status st = launch_finalize(s, u, acc, u_t, stream)) return st;
+    }
+    return ADLBR_OK;
+}
