@@ -331,7 +331,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
-                "gpu_launches": K * 3,  # fused tensor+stencils, operator, finalize
+                # per step: 5 tensor-stage kernels (blur x/y of u, gradient outer product,
+                # blur x/y of J with the D(J) epilogue), the stencil build, the operator
+                # and the finalize kernel
+                "gpu_launches": K * 8,
                 "stages_ms": {"ced_stencils": st_stencils, "explicit_step": st_step},
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24}}

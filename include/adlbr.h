@@ -214,6 +214,87 @@ adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, do
                                  int *iters_out, double *relres_out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Learned preconditioner network (not in the paper): a 3-level U-Net, FP32.
+ *
+ *   enc1: conv3x3(cin->c1) ReLU, conv3x3(c1->c1) ReLU        -> s1 (H x W)
+ *   avgpool 2x2; enc2: conv3x3(c1->c2) ReLU, conv3x3(c2->c2) ReLU -> s2
+ *   avgpool 2x2; mid: conv3x3(c2->c3) ReLU, conv3x3(c3->c3) ReLU
+ *   nearest x2, concat [up, s2]; dec2: conv3x3(c3+c2->c2) ReLU, conv3x3 ReLU
+ *   nearest x2, concat [up, s1]; dec1: conv3x3(c2+c1->c1) ReLU, conv3x3 ReLU
+ *   out: conv1x1(c1->1)
+ * Convolutions are cross-correlations with zero padding.  Parameters: one
+ * flat float vector, per layer in the order above weights [co][ci][ky][kx]
+ * then bias [co].  Tensors: device float [batch][channel][H][W].
+ * ------------------------------------------------------------------------ */
+typedef struct adlbr_unet adlbr_unet; /* opaque: shape and activation buffers */
+
+/* Allocates the activation buffers for `batch` inputs of cin x H x W
+ * (H, W multiples of 4; c1 <= 64). */
+adlbr_status adlbr_unet_create(int cin, int c1, int c2, int c3, int batch, int H, int W,
+                               adlbr_unet **out);
+adlbr_status adlbr_unet_destroy(adlbr_unet *n);
+/* Number of parameters (length of the flat parameter vector). */
+int64_t adlbr_unet_num_params(const adlbr_unet *n);
+/* y [batch][1][H][W] = net(params, x [batch][cin][H][W]); keeps the
+ * activations (and the pointer x) for adlbr_unet_backward. */
+adlbr_status adlbr_unet_forward(adlbr_unet *n, const float *params, const float *x, float *y,
+                                cudaStream_t stream);
+/* Gradient of sum(gy * y) for the last forward: gparams (overwritten, summed
+ * over the batch) and, if gx != NULL, the input gradient gx. */
+adlbr_status adlbr_unet_backward(adlbr_unet *n, const float *params, const float *gy,
+                                 float *gparams, float *gx, cudaStream_t stream);
+/* One Adam update (Kingma & Ba) of n parameters, step count t >= 1. */
+adlbr_status adlbr_adam_step(float *params, const float *grads, float *m, float *v, int64_t n,
+                             double lr, double beta1, double beta2, double eps, int t,
+                             cudaStream_t stream);
+
+/*
+ * Learned preconditioner for adlbr_step_implicit (precond = 1, 2D only):
+ *   M(r) = r / d + s * P(N(F(r))),
+ * d = 1 + dt A_zz, s = rms(r), N the U-Net with cin = 25, batch 1 and
+ * H x W = (ny / 4) x (nx / 4), P the repetition of a coarse value over its
+ * 4 x 4 block, and F(r) the coarse input: the 16 values of r / s in each block
+ * (space to depth, channel 4 dy + dx), then the block means of
+ * log(1 + dt w_k) for the three canonical half-stencil weights and of the
+ * three canonical offsets / 8 (adlbr_stencils_export order).  The solver is
+ * flexible CG (Polak-Ribiere beta); grid extents must be multiples of 16.
+ */
+typedef struct {
+    adlbr_unet *net;
+    const float *params; /* device, adlbr_unet_num_params(net) floats */
+} adlbr_nn_precond;
+
+/*
+ * adlbr_nn_training_pairs -- (residual, error) pairs generated by the solver
+ * for training the preconditioner: CG on (I + dt A) x = rhs from x0 = rhs is
+ * run to convergence (x*), then the system is solved again -- by CG when
+ * nn == NULL, by the preconditioned solver with nn otherwise, so that the
+ * network also sees the residuals it will meet -- and at iterations 0, every,
+ * 2 every, ... (at most max_pairs) the coarse input F(r_k)
+ * [25][ny/4][nx/4] is recorded into feats and the target, the block means of
+ * (x* - x_k - r_k / d) / s_k, [ny/4][nx/4] into targets, i.e. what N should
+ * output at r_k.  xbuf: device float [N] scratch.  *n_pairs receives the
+ * count.  Synchronises.
+ */
+adlbr_status adlbr_nn_training_pairs(adlbr_stencils *s, const float *rhs, double dt, double rtol,
+                                     int maxit, int every, int max_pairs,
+                                     const adlbr_nn_precond *nn, float *feats, float *targets,
+                                     float *xbuf, int *n_pairs, cudaStream_t stream);
+
+/* z = M(r) for the preconditioner above (one application; synchronises). */
+adlbr_status adlbr_nn_precondition(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt,
+                                   const float *r, float *z, cudaStream_t stream);
+
+/* max_z A_zz over the grid (2D), e.g. for the explicit limit dt = 1 / max A_zz.
+ * Synchronises. */
+adlbr_status adlbr_stencils_max_diag(adlbr_stencils *s, double *out, cudaStream_t stream);
+
+/* Mean squared error loss = mean((y - t)^2) over n values (FP64 reduction)
+ * and its gradient gy = 2 (y - t) / n.  loss_out may be NULL (no sync). */
+adlbr_status adlbr_mse_grad(const float *y, const float *t, int64_t n, float *gy,
+                            double *loss_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Coherence-enhancing diffusion (Sec. 4.4, Eq. parabolique), 2D, FP32.
  * ------------------------------------------------------------------------ */
 

@@ -176,3 +176,59 @@ def backward(theta, cache, gy, cin=None, **kw):
         flat.append(gW.ravel())
         flat.append(gb)
     return np.concatenate(flat), gx
+
+
+# ---------------------------------------------------------------- preconditioner
+# The network is used as the coarse part of a preconditioner M for
+# (I + dt A) x = b:  M(r) = r / d + s * P(N(F(r))), where d = 1 + dt A_zz
+# (Jacobi part), s = rms(r), P repeats a coarse value over its RF x RF block,
+# and F(r) are the coarse input channels: the RF^2 values of r / s in each
+# block (space to depth, channel dy * RF + dx) followed by the block means of
+# log(1 + dt w_k) for the three canonical half-stencil weights and of the
+# three canonical offsets / 8.
+RF = 4
+N_STATIC = 9
+N_FEATURES = RF * RF + N_STATIC
+
+
+def restrict(f, rf=RF):
+    C, H, W = f.shape
+    return f.reshape(C, H // rf, rf, W // rf, rf).mean(axis=(2, 4))
+
+
+def space_to_depth(a, rf=RF):
+    H, W = a.shape
+    return a.reshape(H // rf, rf, W // rf, rf).transpose(1, 3, 0, 2).reshape(rf * rf, H // rf, W // rf)
+
+
+def prolong(y, rf=RF):
+    return np.repeat(np.repeat(y, rf, axis=-2), rf, axis=-1)
+
+
+def coarse_features(offs, w, dt, r):
+    """F(r) [N_FEATURES, H/RF, W/RF] and s = rms(r)."""
+    shape = r.shape
+    s = float(np.sqrt(np.mean(np.asarray(r, np.float64) ** 2)))
+    st = np.zeros((N_STATIC,) + shape)
+    for k in range(3):
+        st[k] = np.log1p(dt * w[:, k]).reshape(shape)
+        st[3 + 2 * k] = (offs[:, k, 0] / 8.0).reshape(shape)
+        st[4 + 2 * k] = (offs[:, k, 1] / 8.0).reshape(shape)
+    rs = r / s if s > 0 else np.zeros(shape)
+    return np.concatenate([space_to_depth(rs), restrict(st)]), s
+
+
+def precondition(theta, offs, w, dt, diag, r, **kw):
+    """z = M(r) (see above); diag = A_zz."""
+    f, s = coarse_features(offs, w, dt, r)
+    if s == 0.0:
+        return np.zeros_like(r)
+    y, _ = forward(theta, f, **kw)
+    return r / (1.0 + dt * diag) + s * prolong(y)
+
+
+def training_target(offs, w, dt, diag, r, e):
+    """What the network should output for residual r with error e:
+    R((e - r / d) / s)."""
+    s = float(np.sqrt(np.mean(np.asarray(r, np.float64) ** 2)))
+    return restrict(((e - r / (1.0 + dt * diag)) / s)[None])[0]

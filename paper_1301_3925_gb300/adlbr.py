@@ -67,6 +67,21 @@ def lib():
             "adlbr_step_implicit": (_i32, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
+            "adlbr_unet_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32,
+                                         ctypes.POINTER(_vp)]),
+            "adlbr_unet_destroy": (_i32, [_vp]),
+            "adlbr_unet_num_params": (ctypes.c_int64, [_vp]),
+            "adlbr_unet_forward": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+            "adlbr_unet_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "adlbr_adam_step": (_i32, [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, _i32, _vp]),
+            "adlbr_nn_training_pairs": (_i32, [_vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
+                                               _i32, _i32, _vp, _vp, _vp, _vp,
+                                               ctypes.POINTER(_i32), _vp]),
+            "adlbr_stencils_max_diag": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
+            "adlbr_nn_precondition": (_i32, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+            "adlbr_mse_grad": (_i32, [_vp, _vp, ctypes.c_int64, _vp,
+                                      ctypes.POINTER(ctypes.c_double), _vp]),
             "adlbr_ced_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid)]),
             "adlbr_ced_tensor": (_i32, [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp]),
@@ -166,6 +181,73 @@ def adlbr_step_explicit_noalloc(h, u, u_t, dt, nsteps, stream=None):
                                              _stream(stream)))
 
 
+def adlbr_unet_create(cin, c1, c2, c3, batch, H, W):
+    h = _vp()
+    _check(lib().adlbr_unet_create(cin, c1, c2, c3, batch, H, W, ctypes.byref(h)))
+    return h.value
+
+
+def adlbr_unet_destroy(n):
+    _check(lib().adlbr_unet_destroy(n))
+
+
+def adlbr_unet_num_params(n):
+    return int(lib().adlbr_unet_num_params(n))
+
+
+def adlbr_unet_forward(n, params, x, y, stream=None):
+    _check(lib().adlbr_unet_forward(n, _ptr(params), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def adlbr_unet_backward(n, params, gy, gparams, gx=None, stream=None):
+    _check(lib().adlbr_unet_backward(n, _ptr(params), _ptr(gy), _ptr(gparams), _ptr(gx),
+                                     _stream(stream)))
+
+
+def adlbr_adam_step(params, grads, m, v, n, lr, beta1, beta2, eps, t, stream=None):
+    _check(lib().adlbr_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(n), float(lr),
+                                 float(beta1), float(beta2), float(eps), int(t), _stream(stream)))
+
+
+class NNPrecond(ctypes.Structure):
+    """adlbr_nn_precond: network handle and its device parameter vector."""
+    _fields_ = [("net", _vp), ("params", _vp)]
+
+
+def nn_precond(net, params):
+    return NNPrecond(net, _ptr(params))
+
+
+def adlbr_nn_training_pairs(h, rhs, dt, rtol, maxit, every, max_pairs, nn, feats, targets, xbuf,
+                            stream=None):
+    """Returns the number of pairs written (nn: NNPrecond or None for CG)."""
+    n = ctypes.c_int(0)
+    nnp = ctypes.cast(ctypes.pointer(nn), ctypes.c_void_p).value if nn is not None else None
+    _check(lib().adlbr_nn_training_pairs(h, _ptr(rhs), float(dt), float(rtol), int(maxit),
+                                         int(every), int(max_pairs), nnp, _ptr(feats),
+                                         _ptr(targets), _ptr(xbuf), ctypes.byref(n),
+                                         _stream(stream)))
+    return n.value
+
+
+def adlbr_nn_precondition(h, nn, dt, r, z, stream=None):
+    nnp = ctypes.cast(ctypes.pointer(nn), ctypes.c_void_p).value
+    _check(lib().adlbr_nn_precondition(h, nnp, float(dt), _ptr(r), _ptr(z), _stream(stream)))
+
+
+def adlbr_stencils_max_diag(h, stream=None):
+    v = ctypes.c_double(0.0)
+    _check(lib().adlbr_stencils_max_diag(h, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def adlbr_mse_grad(y, t, n, gy, want_loss=True, stream=None):
+    v = ctypes.c_double(0.0)
+    _check(lib().adlbr_mse_grad(_ptr(y), _ptr(t), int(n), _ptr(gy),
+                                ctypes.byref(v) if want_loss else None, _stream(stream)))
+    return v.value if want_loss else None
+
+
 def adlbr_ced_scratch_bytes(g):
     return int(lib().adlbr_ced_scratch_bytes(ctypes.byref(g)))
 
@@ -197,7 +279,11 @@ def adlbr_step_implicit(h, rhs, x, dt, rtol, maxit, precond=0, nn=None, stream=N
     """Returns (iterations, true relative residual)."""
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
+    if isinstance(nn, NNPrecond):
+        nnp = ctypes.cast(ctypes.pointer(nn), ctypes.c_void_p).value
+    else:
+        nnp = _ptr(nn)
     _check(lib().adlbr_step_implicit(h, _ptr(rhs), _ptr(x), float(dt), float(rtol), int(maxit),
-                                     int(precond), _ptr(nn), ctypes.byref(it), ctypes.byref(rr),
+                                     int(precond), nnp, ctypes.byref(it), ctypes.byref(rr),
                                      _stream(stream)))
     return it.value, rr.value

@@ -142,6 +142,7 @@ adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
     if (s->err) cudaFree(s->err);
     if (s->err_host) cudaFreeHost(s->err_host);
     if (s->ws) cudaFree(s->ws);
+    if (s->ws_nn) cudaFree(s->ws_nn);
     delete s;
     return ADLBR_OK;
 }
@@ -181,9 +182,41 @@ adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, do
     if (adlbr_status st = check_handle(s)) return st;
     if (!rhs || !x) return fail(ADLBR_E_ARG, "null vector");
     if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
+    if (precond == 1)
+        return run_fcg(s, (const float *)rhs, (float *)x, dt, rtol, maxit,
+                       (const adlbr_nn_precond *)nn, iters_out, relres_out, stream);
     if (precond != 0) return fail(ADLBR_E_ARG, "unknown preconditioner %d", precond);
-    (void)nn;
     return run_cg(s, (const float *)rhs, (float *)x, dt, rtol, maxit, iters_out, relres_out, stream);
+}
+
+adlbr_status adlbr_nn_training_pairs(adlbr_stencils *s, const float *rhs, double dt, double rtol,
+                                     int maxit, int every, int max_pairs,
+                                     const adlbr_nn_precond *nn, float *feats, float *targets,
+                                     float *xbuf, int *n_pairs, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!rhs || !feats || !targets || !xbuf) return fail(ADLBR_E_ARG, "null buffer");
+    if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
+    return nn_pairs(s, rhs, dt, rtol, maxit, every, max_pairs, nn, feats, targets, xbuf, n_pairs,
+                    stream);
+}
+
+adlbr_status adlbr_nn_precondition(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt,
+                                   const float *r, float *z, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!r || !z) return fail(ADLBR_E_ARG, "null buffer");
+    return nn_apply(s, nn, dt, r, z, stream);
+}
+
+adlbr_status adlbr_stencils_max_diag(adlbr_stencils *s, double *out, cudaStream_t stream) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!out) return fail(ADLBR_E_ARG, "null output");
+    return max_diag(s, out, stream);
+}
+
+adlbr_status adlbr_mse_grad(const float *y, const float *t, int64_t n, float *gy,
+                            double *loss_out, cudaStream_t stream) {
+    if (!y || !t || !gy || n < 1) return fail(ADLBR_E_ARG, "bad argument");
+    return mse_grad(y, t, n, gy, loss_out, stream);
 }
 
 size_t adlbr_ced_scratch_bytes(const adlbr_grid *g) {

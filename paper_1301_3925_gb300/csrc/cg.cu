@@ -18,12 +18,12 @@
 #include <cstddef>
 
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace adlbr {
 
 namespace {
 
-constexpr int RT = 256;   // threads per reduction block
 constexpr int RB = 1216;  // blocks of the vector kernels (8 per SM on 152 SMs)
 
 struct CgState {
@@ -32,45 +32,47 @@ struct CgState {
     unsigned int count;          // last-block ticket
 };
 
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double warp_part[RT / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_part[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (wid == 0) {
-        s = lane < RT / 32 ? warp_part[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+// (Re)start from the true residual: r = b - (x + dt A x) evaluated in FP64
+// (acc holds dt A x accumulated in FP64), rounded once to FP32; p = r.
+// rr_new = |r|^2 of the FP64 residual, rr = |r|^2 of its FP32 copy, bb = |b|^2;
+// conv = 1 when the true residual already meets the tolerance.
+__global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *__restrict__ b,
+                                                        const float *__restrict__ x,
+                                                        const double *__restrict__ acc,
+                                                        float *__restrict__ r, float *__restrict__ p,
+                                                        double *partials, double *partials2,
+                                                        double *partials3, CgState *S) {
+    double s_true = 0.0, s_rr = 0.0, s_bb = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const double bi = b[i];
+        const double ri = bi - ((double)x[i] + acc[i]);
+        const float rf = (float)ri;
+        r[i] = rf;
+        p[i] = rf;
+        s_true += ri * ri;
+        s_rr += (double)rf * rf;
+        s_bb += bi * bi;
     }
-    __syncthreads();
-    return s;  // valid in thread 0
-}
-
-// Writes this block's partial; returns true in thread 0 of the last block,
-// after which total = sum of all partials in block order.
-__device__ __forceinline__ bool finish_reduction(double part, double *partials, unsigned int *count,
-                                                 double &total) {
-    __shared__ bool last;
+    const double pt = block_sum(s_true);
+    const double pr = block_sum(s_rr);
+    const double pb = block_sum(s_bb);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = part;
-        __threadfence();
-        unsigned int t = atomicAdd(count, 1u);
-        last = (t == gridDim.x - 1);
+        partials2[blockIdx.x] = pr;
+        partials3[blockIdx.x] = pb;
     }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) s += ((volatile double *)partials)[b];
-    s = block_sum(s);
-    if (threadIdx.x == 0) {
-        total = s;
-        *count = 0;
+    double tot;
+    if (finish_reduction(pt, partials, &S->count, tot)) {
+        double rr = 0.0, bb = 0.0;
+        for (int k = 0; k < (int)gridDim.x; ++k) {
+            rr += ((volatile double *)partials2)[k];
+            bb += ((volatile double *)partials3)[k];
+        }
+        S->rr_new = tot;
+        S->rr = rr;
+        S->bb = bb;
+        S->iters = 0;
+        S->conv = (tot <= S->tol2 * bb) ? 1 : 0;
     }
-    return threadIdx.x == 0;
 }
 
 // q <- q + p ; alpha = rr / <p, q>
@@ -127,49 +129,6 @@ __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__
         p[i] = r[i] + beta * p[i];
 }
 
-// (Re)start from the true residual: r = b - (x + dt A x) evaluated in FP64
-// (acc holds dt A x accumulated in FP64), rounded once to FP32; p = r.
-// rr_new = |r|^2 of the FP64 residual, rr = |r|^2 of its FP32 copy, bb = |b|^2;
-// conv = 1 when the true residual already meets the tolerance.
-__global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *__restrict__ b,
-                                                        const float *__restrict__ x,
-                                                        const double *__restrict__ acc,
-                                                        float *__restrict__ r, float *__restrict__ p,
-                                                        double *partials, double *partials2,
-                                                        double *partials3, CgState *S) {
-    double s_true = 0.0, s_rr = 0.0, s_bb = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        const double bi = b[i];
-        const double ri = bi - ((double)x[i] + acc[i]);
-        const float rf = (float)ri;
-        r[i] = rf;
-        p[i] = rf;
-        s_true += ri * ri;
-        s_rr += (double)rf * rf;
-        s_bb += bi * bi;
-    }
-    const double pt = block_sum(s_true);
-    const double pr = block_sum(s_rr);
-    const double pb = block_sum(s_bb);
-    if (threadIdx.x == 0) {
-        partials2[blockIdx.x] = pr;
-        partials3[blockIdx.x] = pb;
-    }
-    double tot;
-    if (finish_reduction(pt, partials, &S->count, tot)) {
-        double rr = 0.0, bb = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) {
-            rr += ((volatile double *)partials2)[k];
-            bb += ((volatile double *)partials3)[k];
-        }
-        S->rr_new = tot;
-        S->rr = rr;
-        S->bb = bb;
-        S->iters = 0;
-        S->conv = (tot <= S->tol2 * bb) ? 1 : 0;
-    }
-}
-
 }  // namespace
 
 struct CgWorkspace {
@@ -216,6 +175,15 @@ static const int *conv_flag(const CgState *S) {
 // on the FP32-rounded residual until the recursive residual meets rtol.
 adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                     int *iters_out, double *relres_out, cudaStream_t st) {
+    return run_cg_hooked(s, b, x, dt, rtol, maxit, iters_out, relres_out, 8, nullptr, nullptr, st);
+}
+
+// As run_cg; when hook != NULL it is called (on the host, work enqueued on
+// st) with the current residual and iterate every `every` iterations of the
+// first CG round, while the solve has not converged.
+adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
+                           int maxit, int *iters_out, double *relres_out, int every, CgHook hook,
+                           void *ctx, cudaStream_t st) {
     CgWorkspace W;
     if (adlbr_status e = cg_workspace(s, W)) return e;
     const int64_t N = s->N;
@@ -244,9 +212,11 @@ adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, doub
         if (relres <= rtol || total_iters >= maxit || restart == kMaxRestarts) break;
         if (restart > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
         prev = relres;
-        const int chunk = 8;
+        const int chunk = every > 0 ? every : 8;
         int it = 0;
         while (it < maxit - total_iters) {
+            if (hook && restart == 0)
+                if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
             for (int k = 0; k < chunk; ++k) {
                 if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), st))
                     return e;

@@ -55,9 +55,11 @@ struct adlbr_stencils {
     void *w;           // device
     int *err;          // device, sticky error bits
     int *err_host;     // pinned host mirror
-    // lazily allocated solver workspace
+    // lazily allocated solver workspaces (CG; learned-preconditioner solver)
     void *ws;
     size_t ws_bytes;
+    void *ws_nn;
+    size_t ws_nn_bytes;
 };
 
 namespace adlbr {
@@ -190,8 +192,32 @@ adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double 
 // (Dtmp, 3N floats, is only used by the fallback path for unusual radii).
 adlbr_status launch_ced_build(adlbr_stencils *s, const float *u, double sigma, double rho,
                               double alpha, double C, void *scratch, float *Dtmp, cudaStream_t st);
+adlbr_status unet_create(int cin, int c1, int c2, int c3, int B, int H, int W, adlbr_unet **out);
+adlbr_status unet_destroy(adlbr_unet *n);
+adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, float *yout,
+                          cudaStream_t st);
+adlbr_status unet_backward(adlbr_unet *n, const float *params, const float *gy, float *gparams,
+                           float *gx, cudaStream_t st);
+adlbr_status unet_adam(float *params, const float *grads, float *m, float *v, int64_t n, double lr,
+                       double b1, double b2, double eps, int t, cudaStream_t st);
+int64_t unet_num_params(const adlbr_unet *n);
+void unet_shape(const adlbr_unet *n, int *cin, int *B, int *H, int *W);
+adlbr_status run_fcg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                     const adlbr_nn_precond *nn, int *iters_out, double *relres_out, cudaStream_t st);
+adlbr_status nn_pairs(adlbr_stencils *s, const float *b, double dt, double rtol, int maxit, int every,
+                      int max_pairs, const adlbr_nn_precond *nn, float *feats, float *targets,
+                      float *xbuf, int *n_pairs, cudaStream_t st);
+adlbr_status max_diag(adlbr_stencils *s, double *out, cudaStream_t st);
+adlbr_status nn_apply(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt, const float *r,
+                      float *z, cudaStream_t st);
+adlbr_status mse_grad(const float *y, const float *t, int64_t n, float *gy, double *loss,
+                      cudaStream_t st);
 adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                     int *iters_out, double *relres_out, cudaStream_t st);
+typedef adlbr_status (*CgHook)(void *ctx, const float *r, const float *x, int iter, cudaStream_t st);
+adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
+                           int maxit, int *iters_out, double *relres_out, int every, CgHook hook,
+                           void *ctx, cudaStream_t st);
 // acc += scale * A u (accumulation type: double for F64 u, float otherwise);
 // a kernel launched with skip != NULL returns at once when *skip != 0.
 adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,

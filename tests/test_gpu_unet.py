@@ -1,0 +1,69 @@
+"""Parity of the CUDA U-Net forward / backward / Adam with the FP64 numpy
+oracle (the learned preconditioner's network; not in the paper)."""
+import numpy as np
+import pytest
+
+from oracle import unet as ou
+from paper_1301_3925_gb300 import adlbr as ab
+
+from gpu_helpers import dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cin,c,B,H,W", [(3, (4, 6, 8), 2, 16, 24), (10, (16, 32, 64), 1, 32, 32)])
+def test_unet_forward_backward_match_oracle(cin, c, B, H, W):
+    t = torch()
+    kw = dict(c1=c[0], c2=c[1], c3=c[2])
+    g = np.random.default_rng(0)
+    theta = ou.init_params(cin, seed=1, **kw) + 0.05 * g.normal(size=ou.n_params(cin, **kw))
+    x = g.normal(size=(B, cin, H, W))
+    gy = g.normal(size=(B, H, W))
+    net = ab.adlbr_unet_create(cin, c[0], c[1], c[2], B, H, W)
+    try:
+        assert ab.adlbr_unet_num_params(net) == theta.size
+        th = dev(theta, t.float32)
+        xd = dev(x.ravel(), t.float32)
+        y = t.empty(B * H * W, dtype=t.float32, device="cuda")
+        ab.adlbr_unet_forward(net, th, xd, y)
+        gth = t.empty_like(th)
+        gx = t.empty_like(xd)
+        ab.adlbr_unet_backward(net, th, dev(gy.ravel(), t.float32), gth, gx)
+        t.cuda.synchronize()
+        yg = y.double().cpu().numpy().reshape(B, H, W)
+        gthg = gth.double().cpu().numpy()
+        gxg = gx.double().cpu().numpy().reshape(B, cin, H, W)
+    finally:
+        ab.adlbr_unet_destroy(net)
+    # the oracle sees the FP32-rounded parameters and inputs
+    th32 = theta.astype(np.float32).astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    gy32 = gy.astype(np.float32).astype(np.float64)
+    gth_ref = np.zeros_like(theta)
+    for b in range(B):
+        yo, cache = ou.forward(th32, x32[b], **kw)
+        assert np.abs(yg[b] - yo).max() <= 1e-4 * max(1.0, np.abs(yo).max())
+        gt, gxo = ou.backward(th32, cache, gy32[b], **kw)
+        gth_ref += gt
+        assert np.abs(gxg[b] - gxo).max() <= 1e-4 * max(1.0, np.abs(gxo).max())
+    # FP32 sums over up to B*H*W terms
+    assert np.abs(gthg - gth_ref).max() <= 2e-4 * max(1.0, np.abs(gth_ref).max())
+
+
+def test_adam_step_matches_formula():
+    t = torch()
+    g = np.random.default_rng(3)
+    n = 1000
+    th, gr, m, v = (g.normal(size=n) for _ in range(4))
+    v = np.abs(v)
+    tt = 7
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    d = [dev(a, t.float32) for a in (th, gr, m, v)]
+    ab.adlbr_adam_step(d[0], d[1], d[2], d[3], n, lr, b1, b2, eps, tt)
+    t.cuda.synchronize()
+    a32 = [a.astype(np.float32).astype(np.float64) for a in (th, gr, m, v)]
+    m2 = b1 * a32[2] + (1 - b1) * a32[1]
+    v2 = b2 * a32[3] + (1 - b2) * a32[1] ** 2
+    th2 = a32[0] - lr * (m2 / (1 - b1 ** tt)) / (np.sqrt(v2 / (1 - b2 ** tt)) + eps)
+    assert np.abs(d[0].double().cpu().numpy() - th2).max() <= 1e-6
+    assert np.abs(d[2].double().cpu().numpy() - m2).max() <= 1e-6

@@ -122,5 +122,72 @@ def test_unet_matches_torch_autograd():
 
 
 def test_unet_param_count():
-    # ~100k parameters with 10 input channels and the default widths
-    assert 100_000 <= unet.n_params(10) <= 130_000
+    # ~100k parameters with the preconditioner's input channels and the default widths
+    assert 100_000 <= unet.n_params(unet.N_FEATURES) <= 130_000
+
+
+def test_space_to_depth_index_map():
+    """Channel dy * RF + dx at coarse (I, J) holds fine value (I RF + dy, J RF + dx)."""
+    RF = unet.RF
+    a = np.random.default_rng(6).normal(size=(3 * RF, 5 * RF))
+    s = unet.space_to_depth(a)
+    assert s.shape == (RF * RF, 3, 5)
+    for I in range(3):
+        for J in range(5):
+            for dy in range(RF):
+                for dx in range(RF):
+                    assert s[dy * RF + dx, I, J] == a[I * RF + dy, J * RF + dx]
+    assert np.allclose(s.mean(axis=0), unet.restrict(a[None])[0], atol=1e-15)
+
+
+def _stencil_field(shape, seed):
+    import oracle
+
+    g = np.random.default_rng(seed)
+    n = shape[0] * shape[1]
+    D = synth.random_spd2(n, seed, kappa_max=20.0)
+    offs, w, st = oracle.build2d(*D)[:3]
+    assert np.all(st == 0)
+    return offs, w, oracle.diag(shape, oracle.NEUMANN, offs, w), g
+
+
+def test_preconditioner_features_and_jacobi_limit():
+    RF = unet.RF
+    shape = (4 * RF, 8 * RF)           # coarse grid divisible by 4 for the U-Net
+    offs, w, diag, g = _stencil_field(shape, 9)
+    dt = 0.7
+    r = g.normal(size=shape)
+    f, s = unet.coarse_features(offs, w, dt, r)
+    assert abs(s - np.sqrt((r ** 2).sum() / r.size)) <= 1e-15 * s
+    assert f.shape == (unet.N_FEATURES, 4, 8)
+    # static channels: block means, by explicit loops over each block
+    for I in range(4):
+        for J in range(8):
+            idx = [(I * RF + dy) * shape[1] + J * RF + dx for dy in range(RF) for dx in range(RF)]
+            for k in range(3):
+                want = np.mean([np.log1p(dt * w[i, k]) for i in idx])
+                assert abs(f[RF * RF + k, I, J] - want) <= 1e-14
+                for c in range(2):
+                    want = np.mean([offs[i, k, c] / 8.0 for i in idx])
+                    assert abs(f[RF * RF + 3 + 2 * k + c, I, J] - want) <= 1e-14
+            assert abs(f[RF + 2, I, J] - r[I * RF + 1, J * RF + 2] / s) <= 1e-14
+    # output layer zeroed: the network adds nothing and M(r) = r / (1 + dt A_zz)
+    theta = unet.init_params(unet.N_FEATURES, seed=1)
+    theta[-17:] = 0.0
+    z = unet.precondition(theta, offs, w, dt, diag, r)
+    assert np.array_equal(z, r / (1.0 + dt * diag))
+    assert np.array_equal(unet.precondition(theta, offs, w, dt, diag, np.zeros(shape)),
+                          np.zeros(shape))
+
+
+def test_training_target_inverts_the_correction():
+    """If the error is r / d + s P(c), the target is c (R P = identity)."""
+    RF = unet.RF
+    shape = (3 * RF, 2 * RF)
+    offs, w, diag, g = _stencil_field(shape, 10)
+    dt = 2.5
+    r = g.normal(size=shape)
+    s = np.sqrt(np.mean(r ** 2))
+    c = g.normal(size=(3, 2))
+    e = r / (1.0 + dt * diag) + s * unet.prolong(c)
+    assert np.abs(unet.training_target(offs, w, dt, diag, r, e) - c).max() <= 1e-13
