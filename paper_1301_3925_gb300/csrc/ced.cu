@@ -9,10 +9,16 @@
 // int(3 s + 0.5) and normalised; every stage reflects its own input about the
 // border (u(-1) = u(0)): the Gaussians and the centred-difference gradient.
 //
-// Kernels: separable Gaussian passes staged through shared memory (a row
-// segment plus halo for the x pass, a column band plus halo for the y pass),
-// the gradient and outer product in one pass, and the 2x2 eigen-
-// decomposition fused into the epilogue of the last (y) pass.
+// Kernels: one fused tile kernel (all stages in shared memory, below), and
+// the separable form it reproduces bit for bit, used where the fused windows
+// do not fit: Gaussian passes staged through shared memory (a row segment
+// plus halo for the x pass, a column band plus halo for the y pass), the
+// gradient and outer product in one pass, and the 2x2 eigen-decomposition
+// fused into the epilogue of the last (y) pass.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
 #include "ced_common.cuh"
 #include "stencil2d.cuh"
 
@@ -166,6 +172,276 @@ adlbr_status separable_tensor(int nx, int ny, const float *u, float *D, int rs, 
     return ADLBR_OK;
 }
 
+// ---- fused tile kernel ---------------------------------------------------
+// One CTA computes D on a FT x FT output tile from a u tile with a halo of
+// R + S + 1 (R, S the radii of K_rho, K_sigma), all intermediate planes in
+// shared memory:
+//   u (reflected loads) -x-> bx -y-> u_sigma -grad, outer-> P -x-> Px -y, D(J)-> D.
+// Every value is computed with the operations, in the order, of the
+// separable kernels above, and every plane is held on an extended window
+// whose cells outside the grid carry the value the separable kernels would
+// read there (their reflected index): for the symmetric blurs of reflected
+// inputs this holds by construction (the taps pair the same two values); P,
+// whose xy component is odd about the border, is evaluated at the reflected
+// cell.  So the fused kernel reproduces the separable result bit for bit.
+// Tiles are full: the last tile of a row or column is shifted back into the
+// grid (its overlap with the previous tile is recomputed and rewritten with
+// the same values).
+constexpr int FT = 64, FNT = 512;
+
+// Window geometry for radii (R, S): P window PH x PW (pitch PP), u_sigma
+// window SH x SW, x-blurred u BH x BW, u window UH x UW; odd pitches keep the
+// lanes of the x passes (one row each) on distinct banks.
+struct FusedGeom {
+    int R, S, PH, PW, PP, SH, SW, SP, BH, BW, BP, UH, UW, UP, XP, nU, offB, offU1, offP;
+    size_t bytes;
+};
+
+__host__ __device__ constexpr FusedGeom fused_geom(int R, int S) {
+    FusedGeom g{};
+    g.R = R, g.S = S;
+    g.PH = g.PW = FT + 2 * R, g.PP = g.PW | 1;
+    g.SH = g.SW = g.PW + 2, g.SP = g.SW | 1;
+    g.BH = g.SH + 2 * S, g.BW = g.SW, g.BP = g.BW | 1;
+    g.UH = g.BH, g.UW = g.SW + 2 * S, g.UP = g.UW | 1;
+    g.XP = FT + 1;
+    // layout [U0][B][U1][P]: the u window of the next tile loads into one U
+    // buffer while the other serves as u, then u_sigma, and Px spans it and B
+    // (both orders are contiguous)
+    int nU = g.UH * g.UP > g.SH * g.SP ? g.UH * g.UP : g.SH * g.SP;
+    const int nB = g.BH * g.BP, nP = 3 * g.PH * g.PP, nX = 3 * g.PH * g.XP;
+    if (nU + nB < nX) nU = nX - nB;
+    g.nU = nU, g.offB = nU, g.offU1 = nU + nB, g.offP = 2 * nU + nB;
+    g.bytes = (size_t)(g.offP + nP) * sizeof(float);
+    return g;
+}
+
+// One output group of a symmetric blur: RB consecutive outputs from the
+// RB + 2r values v (v[r + o] is the centre of output o), in the operation
+// order of the separable kernels.
+template <int RR>
+__device__ __forceinline__ void blur_group(const float (&v)[RB + 2 * RR], const Taps &tp, int r,
+                                           float (&acc)[RB]) {
+#pragma unroll
+    for (int o = 0; o < RB; ++o) acc[o] = __fmul_rn(tp.t[0], v[RR + o]);
+#pragma unroll
+    for (int k = 1; k <= RR; ++k) {
+        if (k > r) break;
+#pragma unroll
+        for (int o = 0; o < RB; ++o) acc[o] = __fmaf_rn(tp.t[k], __fadd_rn(v[RR + o - k], v[RR + o + k]), acc[o]);
+    }
+}
+
+// S_, R_ > 0: radii fixed at compile time (all loops unrolled, windows in
+// registers, constant index arithmetic); 0: taken from g at run time, with
+// the register windows sized for the largest radius kMaxR.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Asynchronous copy of the (reflected) u window of the tile at (x0, y0).
+template <int S_, int R_>
+__device__ __forceinline__ void load_u_window(const FusedGeom &g, int nx, int ny, int x0, int y0,
+                                              const float *__restrict__ u, float *U) {
+    const int uox = x0 - g.R - 1 - g.S, uoy = y0 - g.R - 1 - g.S;
+    const bool interior = uox >= 0 && uoy >= 0 && uox + g.UW <= nx && uoy + g.UH <= ny;
+    for (int i = threadIdx.x; i < g.UH * g.UW; i += FNT) {
+        const int r = i / g.UW, c = i - r * g.UW;
+        const int gy = interior ? uoy + r : reflect(uoy + r, ny);
+        const int gx = interior ? uox + c : reflect(uox + c, nx);
+        cp_async4(U + r * g.UP + c, u + (int64_t)gy * nx + gx);
+    }
+    cp_async_commit();
+}
+
+// S_, R_ > 0: radii fixed at compile time (all loops unrolled, windows in
+// registers, constant index arithmetic); 0: taken from g at run time, with
+// the register windows sized for the largest radius kMaxR.
+// Persistent: CTA b processes tiles b, b + gridDim.x, ...; the u window of
+// the next tile is copied asynchronously while the current one is computed.
+template <int S_, int R_>
+__global__ void __launch_bounds__(FNT, 1) ced_fused_kernel(int nx, int ny, int64_t N, FusedGeom gr, Taps ts,
+                                                           Taps tr, const float *__restrict__ u,
+                                                           float *__restrict__ D, float alpha, float Cc) {
+    constexpr bool fixed = S_ > 0 && R_ > 0;
+    constexpr FusedGeom gc = fused_geom(R_ > 0 ? R_ : 1, S_ > 0 ? S_ : 1);
+    const FusedGeom &g = fixed ? gc : gr;
+    constexpr int SR = fixed ? S_ : kMaxR, RR = fixed ? R_ : kMaxR;   // register window radii
+    extern __shared__ float sm[];
+    float *B = sm + g.offB, *P = sm + g.offP;
+    const int R = g.R, S = g.S;
+    const int tiles_x = (nx + FT - 1) / FT, tiles = tiles_x * ((ny + FT - 1) / FT);
+    int tile = blockIdx.x;
+    if (tile >= tiles) return;
+    auto origin = [&](int t, int &x0, int &y0) {
+        x0 = min((t % tiles_x) * FT, nx - FT);
+        y0 = min((t / tiles_x) * FT, ny - FT);
+    };
+    {
+        int x0, y0;
+        origin(tile, x0, y0);
+        load_u_window<S_, R_>(g, nx, ny, x0, y0, u, sm);
+    }
+    for (int it = 0; tile < tiles; tile += gridDim.x, ++it) {
+    float *U = (it & 1) ? sm + g.offU1 : sm;
+    float *US = U, *PX = (it & 1) ? B : sm;   // u_sigma over u; Px over u and bx
+    int x0, y0;
+    origin(tile, x0, y0);
+    // window origins (grid coordinates of local (0, 0))
+    const int pox = x0 - R, poy = y0 - R;            // P
+    const int sox = pox - 1, soy = poy - 1;          // u_sigma; bx has its columns
+    const int uox = sox - S, uoy = soy - S;          // u; bx has its rows
+    const bool interior = uox >= 0 && uoy >= 0 && uox + g.UW <= nx && uoy + g.UH <= ny;
+    cp_async_wait_all();
+    __syncthreads();   // u of this tile is in place; the previous tile is done
+    if (tile + (int)gridDim.x < tiles) {
+        int nx0, ny0;
+        origin(tile + gridDim.x, nx0, ny0);
+        load_u_window<S_, R_>(g, nx, ny, nx0, ny0, u, (it & 1) ? sm : sm + g.offU1);
+    }
+    // 2. bx = x pass of u (lanes along rows, RB outputs per thread)
+    {
+        const int groups = (g.BW + RB - 1) / RB;
+        for (int i = threadIdx.x; i < g.BH * groups; i += FNT) {
+            const int r = i % g.BH, c0 = (i / g.BH) * RB;
+            const float *s = U + r * g.UP + c0 + S - SR;
+            float v[RB + 2 * SR], acc[RB];
+#pragma unroll
+            for (int j = 0; j < RB + 2 * SR; ++j) v[j] = (fixed || (j >= SR - S && j < SR + S + RB)) ? s[j] : 0.f;
+            blur_group<SR>(v, ts, S, acc);
+#pragma unroll
+            for (int o = 0; o < RB; ++o)
+                if (c0 + o < g.BW) B[r * g.BP + c0 + o] = acc[o];
+        }
+    }
+    __syncthreads();
+    // 3. u_sigma = y pass of bx (lanes along columns, RB rows per thread)
+    {
+        const int groups = (g.SH + RB - 1) / RB;
+        for (int i = threadIdx.x; i < g.SW * groups; i += FNT) {
+            const int c = i % g.SW, r0 = (i / g.SW) * RB;
+            const float *s = B + (r0 + S - SR) * g.BP + c;
+            float v[RB + 2 * SR], acc[RB];
+#pragma unroll
+            for (int j = 0; j < RB + 2 * SR; ++j)
+                v[j] = (fixed || (j >= SR - S && j < SR + S + RB)) ? s[j * g.BP] : 0.f;
+            blur_group<SR>(v, ts, S, acc);
+#pragma unroll
+            for (int o = 0; o < RB; ++o)
+                if (r0 + o < g.SH) US[(r0 + o) * g.SP + c] = acc[o];
+        }
+    }
+    __syncthreads();
+    // 4. P = outer product of the centred differences, at the reflected cell
+    for (int i = threadIdx.x; i < g.PH * g.PW; i += FNT) {
+        const int r = i / g.PW, c = i - r * g.PW;
+        const int ly = (interior ? poy + r : reflect(poy + r, ny)) - soy;
+        const int lx = (interior ? pox + c : reflect(pox + c, nx)) - sox;
+        const float *s = US + ly * g.SP + lx;
+        const float gx = __fmul_rn(0.5f, __fsub_rn(s[1], s[-1]));
+        const float gy = __fmul_rn(0.5f, __fsub_rn(s[g.SP], s[-g.SP]));
+        P[r * g.PP + c] = __fmul_rn(gx, gx);
+        P[(g.PH + r) * g.PP + c] = __fmul_rn(gx, gy);
+        P[(2 * g.PH + r) * g.PP + c] = __fmul_rn(gy, gy);
+    }
+    __syncthreads();
+    // 5. Px = x pass of P over the FT output columns (lanes along rows)
+    {
+        constexpr int groups = FT / RB;
+        for (int i = threadIdx.x; i < g.PH * groups; i += FNT) {
+            const int r = i % g.PH, c0 = (i / g.PH) * RB;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float *s = P + (ch * g.PH + r) * g.PP + c0 + R - RR;
+                float v[RB + 2 * RR], acc[RB];
+#pragma unroll
+                for (int j = 0; j < RB + 2 * RR; ++j)
+                    v[j] = (fixed || (j >= RR - R && j < RR + R + RB)) ? s[j] : 0.f;
+                blur_group<RR>(v, tr, R, acc);
+#pragma unroll
+                for (int o = 0; o < RB; ++o) PX[(ch * g.PH + r) * g.XP + c0 + o] = acc[o];
+            }
+        }
+    }
+    __syncthreads();
+    // 6. y pass of Px and D(J) (lanes along columns, RB rows per thread)
+    {
+        constexpr int groups = FT / RB;
+        for (int i = threadIdx.x; i < FT * groups; i += FNT) {
+            const int c = i % FT, r0 = (i / FT) * RB;
+            float J[3][RB];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float *s = PX + (ch * g.PH + r0 + R - RR) * g.XP + c;
+                float v[RB + 2 * RR];
+#pragma unroll
+                for (int j = 0; j < RB + 2 * RR; ++j)
+                    v[j] = (fixed || (j >= RR - R && j < RR + R + RB)) ? s[j * g.XP] : 0.f;
+                blur_group<RR>(v, tr, R, J[ch]);
+            }
+#pragma unroll
+            for (int o = 0; o < RB; ++o) {
+                const int64_t z = (int64_t)(y0 + r0 + o) * nx + x0 + c;
+                float dxx, dxy, dyy;
+                d_from_j(J[0][o], J[1][o], J[2][o], alpha, Cc, dxx, dxy, dyy);
+                D[z] = dxx;
+                D[N + z] = dxy;
+                D[2 * N + z] = dyy;
+            }
+        }
+    }
+    }
+}
+
+// Kernel choice: the fused tile kernel where it applies, else the separable
+// passes.  ADLBR_CED_PATH=separable in the environment forces the separable
+// passes (the two are bit-identical; the tests compare them).
+int ced_path() {
+    const char *e = getenv("ADLBR_CED_PATH");
+    return (e && strcmp(e, "separable") == 0) ? 1 : 0;
+}
+
+// The fused kernel needs full tiles, reflections that stay inside the
+// windows (grid sides >= FT) and windows that fit in shared memory.
+bool fused_ok(int nx, int ny, int R, int S) {
+    if (nx < FT || ny < FT) return false;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    return fused_geom(R, S).bytes <= (size_t)optin;
+}
+
+template <int S_, int R_>
+adlbr_status launch_fused(int nx, int ny, const FusedGeom &g, const float *u, float *D, const Taps &ts,
+                          const Taps &tr, float alpha, float C, cudaStream_t st) {
+    ADLBR_CUDA(cudaFuncSetAttribute(ced_fused_kernel<S_, R_>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes));
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        ADLBR_CUDA(cudaGetDevice(&dev));
+        ADLBR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int tiles = (int)(blocks_for(nx, FT) * blocks_for(ny, FT));
+    const int grid = std::min(tiles, sms);
+    ced_fused_kernel<S_, R_><<<grid, FNT, g.bytes, st>>>(nx, ny, (int64_t)nx * ny, g, ts, tr, u, D,
+                                                         alpha, C);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status fused_tensor(int nx, int ny, const float *u, float *D, int rs, int rr, const Taps &ts,
+                          const Taps &tr, float alpha, float C, cudaStream_t st) {
+    const FusedGeom g = fused_geom(rr, rs);
+    if (rs == 3 && rr == 12)   // sigma = 1, rho = 4
+        return launch_fused<3, 12>(nx, ny, g, u, D, ts, tr, alpha, C, st);
+    return launch_fused<0, 0>(nx, ny, g, u, D, ts, tr, alpha, C, st);
+}
+
 adlbr_status check_params(double sigma, double rho, double alpha, double C) {
     if (!(sigma > 0) || !(rho > 0) || !(alpha > 0 && alpha <= 1) || !(C >= 0))
         return fail(ADLBR_E_ARG, "bad CED parameters");
@@ -181,8 +457,12 @@ size_t ced_tensor_scratch_bytes(int64_t N) { return (size_t)N * sizeof(float) * 
 adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double sigma, double rho,
                                double alpha, double C, void *scratch, cudaStream_t st) {
     if (adlbr_status e = check_params(sigma, rho, alpha, C)) return e;
-    return separable_tensor(nx, ny, u, D, radius_of(sigma), radius_of(rho), make_taps(sigma),
-                            make_taps(rho), (float)alpha, (float)C, scratch, st);
+    const int rs = radius_of(sigma), rr = radius_of(rho);
+    if (ced_path() != 1 && fused_ok(nx, ny, rr, rs))
+        return fused_tensor(nx, ny, u, D, rs, rr, make_taps(sigma), make_taps(rho), (float)alpha,
+                            (float)C, st);
+    return separable_tensor(nx, ny, u, D, rs, rr, make_taps(sigma), make_taps(rho), (float)alpha,
+                            (float)C, scratch, st);
 }
 
 adlbr_status launch_ced_build(adlbr_stencils *s, const float *u, double sigma, double rho,
