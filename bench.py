@@ -34,6 +34,9 @@ UNIT = "Gpts/s"
 N_SIDE = 4096
 CED = dict(sigma=1.0, rho=4.0, alpha=1e-4, C=1e-5, dt=0.02)
 SEED = 1
+# DRAM bytes (read + write) of one launch at 4096^2, from ncu captures of the
+# current kernels (the summaries under profiles/ give the commands)
+TRAFFIC_4096 = {"ced_fused_kernel": 67.17e6 + 140.37e6, "build2d_kernel": 201.50e6 + 229.51e6}
 
 
 def parse():
@@ -44,6 +47,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-implicit", action="store_true", help="skip the implicit-step measurement")
+    p.add_argument("--no-3d", action="store_true", help="skip the 3D measurement and precision study")
+    p.add_argument("--precision-steps", type=int, default=100)
     return p.parse_args()
 
 
@@ -132,6 +138,134 @@ def allmax(ws, x):
     t = torch.tensor([x], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def time_ms(fn, reps, stream):
+    """Mean device time of fn() over reps calls (CUDA events on `stream`)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+# ----------------------------------------------------------------- sub-measurements
+def implicit_measurement(peak):
+    """Implicit step (I + dt A) x = u_n on 2048^2, smooth random orientation,
+    kappa in [1, 50], dt = 200 / max A_zz, tolerance 1e-6: plain CG, flexible
+    CG with the Jacobi part of the preconditioner alone, and flexible CG with
+    the trained U-Net preconditioner (trained here on three other right-hand
+    sides of the same operator; training time reported separately)."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    from paper_1301_3925_gb300 import nn
+    n = 2048
+    D = torch.from_numpy(synth.smooth_field2d(n, n, 3, 1.0, 50.0, 16).reshape(3, -1)
+                         .astype(np.float32)).cuda()
+    g = ab.grid((n, n))
+    h = ab.adlbr_build_stencils(g, D, ab.F32, ab.F32)
+    try:
+        dt = 200.0 / ab.adlbr_stencils_max_diag(h)
+        b = torch.from_numpy(synth.u_uniform((n, n), 3).astype(np.float32).ravel()).cuda()
+        x = torch.empty_like(b)
+        out = {"grid": [n, n], "dt": dt, "rtol": 1e-6, "rhs": "U[0,1] seed 3",
+               "field": "smooth orientation, kappa in [1, 50], 16x16 lattice, seed 3"}
+
+        def solve(precond=0, desc=None):
+            x.copy_(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, rel = ab.adlbr_step_implicit(h, b, x, dt, 1e-6, 4000, precond=precond, nn=desc)
+            torch.cuda.synchronize()
+            fb = ab.adlbr_last_fallback() if precond else 0
+            return it, rel, (time.perf_counter() - t0) * 1e3, fb
+
+        solve()
+        cg = [solve() for _ in range(3)]
+        out["cg"] = {"iters": cg[-1][0], "relres": cg[-1][1], "ms": float(np.median([c[2] for c in cg]))}
+        t0 = time.perf_counter()
+        rhs = [torch.from_numpy(synth.u_uniform((n, n), 100 + k).astype(np.float32).ravel()).cuda()
+               for k in range(3)]
+        params, log = nn.fit(h, rhs, dt, rounds=3, steps=(1500, 700, 700), crop=48)
+        torch.cuda.synchronize()
+        out["train_s"] = time.perf_counter() - t0
+        out["train_loss"] = [r["loss"][-1][1] for r in log]
+        jac = params.clone()
+        jac[-17:] = 0.0
+        for name, th in (("jacobi_fcg", jac), ("nn_fcg", params)):
+            pc = nn.Preconditioner(th, n, n)
+            try:
+                solve(1, pc.desc)
+                r = [solve(1, pc.desc) for _ in range(3)]
+            finally:
+                pc.close()
+            out[name] = {"iters": r[-1][0], "relres": r[-1][1], "ms": float(np.median([c[2] for c in r])),
+                         "fell_back_to_cg": bool(r[-1][3])}
+        out["nn_vs_cg_wallclock"] = out["cg"]["ms"] / out["nn_fcg"]["ms"]
+        return out
+    finally:
+        ab.adlbr_stencils_destroy(h)
+
+
+def volume_measurement(peak, steps):
+    """3D 256^3 needle field (eigenvalues 1, 1/400, 1/400, smooth random
+    orientation on a 16^3 lattice, seed 2): stencil build, operator and
+    explicit-step throughput, and the precision study: `steps` explicit steps
+    at dt = 1 / max A_zz with u in FP64, FP32 and BF16 (FP16 weights for the
+    FP32 / BF16 runs, FP64 weights for the FP64 run), errors relative to the
+    FP64 run."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    n = 256
+    N = n ** 3
+    D = torch.from_numpy(synth.needle_field3d(n, 2, dtype=np.float32).reshape(6, -1)).cuda()
+    g = ab.grid((n, n, n))
+    st = torch.cuda.current_stream()
+    out = {"grid": [n, n, n], "field": "needle, kappa 20, 16^3 lattice, seed 2"}
+    h16 = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+    h64 = ab.adlbr_build_stencils(g, D, ab.F32, ab.F64)
+    try:
+        ms = time_ms(lambda: ab.adlbr_build_stencils(g, D, ab.F32, ab.F16, out=h16), 5, st)
+        out["build_ms"] = ms
+        out["build_gpts"] = N / (ms * 1e-3) / 1e9
+        u0 = synth.u_uniform((n, n, n), 2).ravel()
+        u32 = torch.from_numpy(u0.astype(np.float32)).cuda()
+        Au = torch.empty_like(u32)
+        ms = time_ms(lambda: ab.adlbr_apply(h16, u32, Au, ab.F32), 10, st)
+        # u in (4), offsets (12), weights (6 x f16 + scale lane = 16), Au out (4)
+        gbs = 36 * N / (ms * 1e-3) / 1e9
+        out["apply"] = {"ms": ms, "gpts": N / (ms * 1e-3) / 1e9, "gbs": gbs, "frac_hbm": gbs / peak,
+                        "bytes_per_point": 36}
+        dt = 1.0 / ab.adlbr_stencils_max_diag(h64)
+        out["dt"] = dt
+        runs = {}
+        for name, h, dtype, code in (("f64", h64, torch.float64, ab.F64), ("f32", h16, torch.float32, ab.F32),
+                                     ("bf16", h16, torch.bfloat16, ab.BF16)):
+            u = torch.from_numpy(u0).cuda().to(dtype)
+            scratch = torch.empty(ab.adlbr_step_scratch_bytes(h, code), dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ab.adlbr_step_explicit(h, u, scratch, code, dt, steps)
+            torch.cuda.synchronize()
+            runs[name] = (u.double(), (time.perf_counter() - t0) * 1e3 / steps)
+        ref = runs["f64"][0]
+        scale = ref.abs().max().item()
+        out["precision"] = {"steps": steps}
+        for name, (u, ms) in runs.items():
+            out["precision"][name] = {"ms_per_step": ms,
+                                      "rel_linf_vs_f64": (u - ref).abs().max().item() / scale}
+        return out
+    finally:
+        ab.adlbr_stencils_destroy(h16)
+        ab.adlbr_stencils_destroy(h64)
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -231,11 +365,14 @@ def main():
     acc = scratch[9 * N * 4: 10 * N * 4].view(torch.float32)
     stream = torch.cuda.current_stream()
     h = None
+    S = (CED["sigma"], CED["rho"], CED["alpha"], CED["C"])
 
     def step():
+        # adlbr_ced_stencils (tensor stage + stencil build) as its two calls,
+        # so that each kernel is timed on its own; then the explicit step
         nonlocal h
-        h = ab.adlbr_ced_stencils(h, g, u, scratch, CED["sigma"], CED["rho"], CED["alpha"], CED["C"],
-                                  ab.F16)
+        ab.adlbr_ced_tensor(g, u, Dbuf, *S, scratch)
+        h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
         ab.adlbr_step_explicit(h, u, acc, ab.F32, CED["dt"], 1)
 
     for _ in range(max(args.warmup, 3)):
@@ -244,7 +381,7 @@ def main():
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -261,11 +398,12 @@ def main():
     for k in range(K):
         e = ev[k]
         e[0].record(stream)
-        h = ab.adlbr_ced_stencils(h, g, u, scratch, CED["sigma"], CED["rho"], CED["alpha"], CED["C"],
-                                  ab.F16)
+        ab.adlbr_ced_tensor(g, u, Dbuf, *S, scratch)
         e[1].record(stream)
-        ab.adlbr_step_explicit(h, u, acc, ab.F32, CED["dt"], 1)
+        h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
         e[2].record(stream)
+        ab.adlbr_step_explicit(h, u, acc, ab.F32, CED["dt"], 1)
+        e[3].record(stream)
     end.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -274,26 +412,38 @@ def main():
     ab.adlbr_stencils_check(h)
     total_ms = start.elapsed_time(end)
     total_ms = allmax(ws, total_ms)
-    st_stencils = np.mean([e[0].elapsed_time(e[1]) for e in ev])
-    st_step = np.mean([e[1].elapsed_time(e[2]) for e in ev])
+    st_tensor = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    st_build = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    st_step = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
     ms_step = total_ms / K
     value = ws * N / (ms_step * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (algorithmic bytes per point of each stage)
+    # roofline of the dominant kernel (algorithmic bytes per point of each)
     peak, peak_src = measured_peaks()
     stages = {
-        # u in; offsets (int16 x 4) + weights (4 x f16) out
-        "ced_stencils": (st_stencils, 4 + 8 + 8),
-        # u in, u out, stencil in
-        "explicit_step": (st_step, 4 + 4 + 16),
+        # u in; D (3 x f32) out
+        "ced_fused_kernel": (st_tensor, 4 + 12),
+        # D in; offsets (int16 x 4) + weights (4 x f16) out
+        "build2d_kernel": (st_build, 12 + 8 + 8),
+        # operator + finalize: u in, stencil in, u out
+        "explicit_step": (st_step, 4 + 16 + 4),
     }
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms, dom_bpp = stages[dom]
     achieved = dom_bpp * N / (dom_ms * 1e-3) / 1e9
+    traffic = TRAFFIC_4096.get(dom)
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-            "bytes_per_point": dom_bpp}
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+            "bytes_per_point": dom_bpp, "units_per_launch": N}
     step_gbs = 24 * N / (st_step * 1e-3) / 1e9
+
+    # the operator alone on the step's stencils (adlbr_apply: zero Au, accumulate)
+    Au = torch.empty_like(u)
+    apply_ms = time_ms(lambda: ab.adlbr_apply(h, u, Au, ab.F32), 20, stream)
+    apply_gbs = 24 * N / (apply_ms * 1e-3) / 1e9
+    apply_sub = {"ms": apply_ms, "gpts": N / (apply_ms * 1e-3) / 1e9, "gbs": apply_gbs,
+                 "frac_hbm": apply_gbs / peak, "bytes_per_point": 24,
+                 "stencils": "CED kappa <= 100 (4096^2 fingerprint)"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -320,6 +470,9 @@ def main():
         e2e = {"value": ws * N / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N}
 
+    implicit = None if args.no_implicit or rank != 0 else implicit_measurement(peak)
+    volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline()
@@ -331,13 +484,13 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
-                # per step: 5 tensor-stage kernels (blur x/y of u, gradient outer product,
-                # blur x/y of J with the D(J) epilogue), the stencil build, the operator
+                # per step: the fused tensor kernel, the stencil build, the operator
                 # and the finalize kernel
-                "gpu_launches": K * 8,
-                "stages_ms": {"ced_stencils": st_stencils, "explicit_step": st_step},
+                "gpu_launches": K * 4,
+                "stages_ms": {"tensor": st_tensor, "build": st_build, "explicit_step": st_step},
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
-                                  "frac_hbm": step_gbs / peak, "bytes_per_point": 24}}
+                                  "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
+                "apply": apply_sub, "implicit": implicit, "volume3d": volume}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:

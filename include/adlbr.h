@@ -201,7 +201,12 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  *  rhs         device float [N].
  *  x           device float [N]: initial guess on entry, solution on exit.
  *  precond     0: plain CG.  1: flexible CG preconditioned by the U-Net of
- *              adlbr_unet_* with parameters nn (see below).
+ *              adlbr_unet_* with parameters nn (see below).  Plain CG is its
+ *              fallback: when the preconditioned recursive residual grows
+ *              tenfold above its best value or does not halve within 100
+ *              iterations, the solve restarts from the initial guess with
+ *              plain CG (iters_out then counts both; adlbr_last_fallback()
+ *              returns 1).
  *  nn          preconditioner parameters (precond == 1), else ignored.
  *  iters_out   iterations performed (may be NULL).
  *  relres_out  final true relative residual |rhs - (I + dt A) x| / |rhs|.
@@ -212,6 +217,10 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
 adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, double dt,
                                  double rtol, int maxit, int precond, const void *nn,
                                  int *iters_out, double *relres_out, cudaStream_t stream);
+
+/* 1 if the last preconditioned adlbr_step_implicit call of this thread fell
+ * back to plain CG, else 0 (thread-local; not in the paper). */
+int adlbr_last_fallback(void);
 
 /* ------------------------------------------------------------------------
  * Learned preconditioner network (not in the paper): a 3-level U-Net, FP32.
@@ -285,8 +294,8 @@ adlbr_status adlbr_nn_training_pairs(adlbr_stencils *s, const float *rhs, double
 adlbr_status adlbr_nn_precondition(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt,
                                    const float *r, float *z, cudaStream_t stream);
 
-/* max_z A_zz over the grid (2D), e.g. for the explicit limit dt = 1 / max A_zz.
- * Synchronises. */
+/* max_z A_zz over the grid (2D or 3D; FP32 accumulation), e.g. for the
+ * explicit limit dt = 1 / max A_zz.  Synchronises. */
 adlbr_status adlbr_stencils_max_diag(adlbr_stencils *s, double *out, cudaStream_t stream);
 
 /* Mean squared error loss = mean((y - t)^2) over n values (FP64 reduction)

@@ -67,6 +67,7 @@ def lib():
             "adlbr_step_implicit": (_i32, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
+            "adlbr_last_fallback": (_i32, []),
             "adlbr_unet_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32,
                                          ctypes.POINTER(_vp)]),
             "adlbr_unet_destroy": (_i32, [_vp]),
@@ -287,3 +288,8 @@ def adlbr_step_implicit(h, rhs, x, dt, rtol, maxit, precond=0, nn=None, stream=N
                                      int(precond), nnp, ctypes.byref(it), ctypes.byref(rr),
                                      _stream(stream)))
     return it.value, rr.value
+
+
+def adlbr_last_fallback():
+    """1 if the last preconditioned implicit solve of this thread fell back to plain CG."""
+    return int(lib().adlbr_last_fallback())

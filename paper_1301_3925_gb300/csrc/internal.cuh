@@ -118,6 +118,29 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(flo
     return __ushort_as_bfloat16(f2bf_bits(v));
 }
 
+// Selling offsets of a 3D superbase (e0 = -e1-e2-e3): pair q = (i, j) gets
+// e_k x e_l with {k, l} the complement, q in (01, 02, 03, 12, 13, 23).
+__device__ __forceinline__ void selling_offsets(const char4 (&b)[3], int (&c)[6][3]) {
+    int e[4][3];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        e[k][0] = b[k - 1].x;
+        e[k][1] = b[k - 1].y;
+        e[k][2] = b[k - 1].z;
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) e[0][t] = -e[1][t] - e[2][t] - e[3][t];
+    constexpr int PK[6] = {2, 1, 1, 0, 0, 0};
+    constexpr int PL[6] = {3, 3, 2, 3, 2, 1};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const int *a = e[PK[q]], *bb = e[PL[q]];
+        c[q][0] = a[1] * bb[2] - a[2] * bb[1];
+        c[q][1] = a[2] * bb[0] - a[0] * bb[2];
+        c[q][2] = a[0] * bb[1] - a[1] * bb[0];
+    }
+}
+
 // ---------------------------------------------------------------- weights
 // Reads the K weights of point i (widened to Acc) and the zero mask.
 template <typename Acc, int K>

@@ -66,6 +66,39 @@ __global__ void diag2d_kernel(int nx, int ny, int bc, const short4 *__restrict__
     atomicAdd(d + z, own);
 }
 
+// 3D: every in-grid pair (z, z +- c_q) of the six Selling offsets adds w_q
+// at both ends
+__global__ void diag3d_kernel(int nx, int ny, int nz, int bc, const char4 *__restrict__ offs,
+                              const void *__restrict__ wbase, adlbr_dtype wt, float *__restrict__ d) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, zc = blockIdx.z;
+    if (x >= nx) return;
+    const int64_t z = ((int64_t)zc * ny + y) * nx + x;
+    const char4 b[3] = {offs[3 * z], offs[3 * z + 1], offs[3 * z + 2]};
+    int c[6][3];
+    selling_offsets(b, c);
+    float w[6];
+    load_weights<float, 6>(wbase, wt, z, w);
+    float own = 0.f;
+    for (int q = 0; q < 6; ++q) {
+        if (w[q] == 0.f) continue;
+        for (int s = -1; s <= 1; s += 2) {
+            int xn = x + s * c[q][0], yn = y + s * c[q][1], zn = zc + s * c[q][2];
+            if (bc == ADLBR_PERIODIC) {
+                xn = ((xn % nx) + nx) % nx;
+                yn = ((yn % ny) + ny) % ny;
+                zn = ((zn % nz) + nz) % nz;
+            } else if (xn < 0 || xn >= nx || yn < 0 || yn >= ny || zn < 0 || zn >= nz) {
+                continue;
+            }
+            const int64_t zz = ((int64_t)zn * ny + yn) * nx + xn;
+            if (zz == z) continue;
+            own += w[q];
+            atomicAdd(d + zz, w[q]);
+        }
+    }
+    atomicAdd(d + z, own);
+}
+
 // d <- 1 + dt d ; max of d over the grid into *dmax (as ordered bits; d >= 0)
 __global__ void diag_finish_kernel(int64_t N, float dt, float *__restrict__ d, unsigned *dmax_bits) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,8 +413,12 @@ static adlbr_status compute_diag(adlbr_stencils *s, NnWorkspace &W, double dt, d
     ADLBR_CUDA(cudaMemsetAsync(W.d, 0, s->N * sizeof(float), st));
     ADLBR_CUDA(cudaMemsetAsync(W.dmax, 0, sizeof(unsigned), st));
     dim3 g(blocks_for(s->n[0], 256), (unsigned)s->n[1]);
-    diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs, s->w,
-                                     s->w_t, W.d);
+    if (s->dim == 2)
+        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs,
+                                         s->w, s->w_t, W.d);
+    else
+        diag3d_kernel<<<dim3(blocks_for(s->n[0], 128), (unsigned)s->n[1], (unsigned)s->n[2]), 128, 0, st>>>(
+            (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (const char4 *)s->offs, s->w, s->w_t, W.d);
     diag_finish_kernel<<<blocks_for(s->N, 256), 256, 0, st>>>(s->N, (float)dt, W.d, W.dmax);
     ADLBR_CUDA(cudaGetLastError());
     if (dmax_host) {
@@ -433,6 +470,8 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
                                    double *relres_out, int every, CgHook hook, void *ctx,
                                    cudaStream_t st);
 
+static thread_local int g_fallback = 0;
+
 adlbr_status run_fcg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                      const adlbr_nn_precond *nn, int *iters_out, double *relres_out, cudaStream_t st) {
     return run_fcg_hooked(s, b, x, dt, rtol, maxit, nn, iters_out, relres_out, 2, nullptr, nullptr, st);
@@ -464,6 +503,18 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     FcgState host = {};
     const int chunk = every > 0 ? every : 2;
     int it = 0;
+    // Plain CG is the fallback of a user solve: the initial guess is kept, and
+    // when the recursive residual of the preconditioned solve grows tenfold
+    // above its best value, or fails to halve within kStall iterations, the
+    // solve restarts from it with plain CG.
+    constexpr int kStall = 100;
+    if (!hook) {
+        g_fallback = 0;
+        ADLBR_CUDA(cudaMemcpyAsync(W.xs, x, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    double best = INFINITY;
+    int best_it = 0;
+    bool fall_back = false;
     while (it < maxit) {
         if (hook)
             if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
@@ -479,6 +530,22 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
         if (host.conv) break;
+        if (!hook) {
+            const double rel = host.bb > 0 ? std::sqrt(host.rr / host.bb) : 0.0;
+            if (rel < 0.5 * best) best = rel, best_it = it;
+            if (!(rel <= 10.0 * best) || it - best_it >= kStall) {
+                fall_back = true;
+                break;
+            }
+        }
+    }
+    if (fall_back) {
+        g_fallback = 1;
+        ADLBR_CUDA(cudaMemcpyAsync(x, W.xs, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        int cg_it = 0;
+        const adlbr_status e = run_cg(s, b, x, dt, rtol, std::max(1, maxit - it), &cg_it, relres_out, st);
+        if (iters_out) *iters_out = it + cg_it;
+        return e;
     }
     // true residual with the operator accumulated in FP64 (q and z hold 8N bytes)
     double *acc64 = (double *)W.q;
@@ -497,6 +564,8 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
                     host.iters, relres);
     return ADLBR_OK;
 }
+
+extern "C" int adlbr_last_fallback(void) { return g_fallback; }
 
 // ---------------------------------------------------------------- training pairs
 namespace {
@@ -600,7 +669,6 @@ adlbr_status nn_apply(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt, 
 }
 
 adlbr_status max_diag(adlbr_stencils *s, double *out, cudaStream_t st) {
-    if (s->dim != 2) return fail(ADLBR_E_SHAPE, "2D only");
     NnWorkspace W;
     if (adlbr_status e = nn_workspace(s, W)) return e;
     return compute_diag(s, W, 0.0, out, st);

@@ -67,29 +67,34 @@ def _lattice_coords(n, m):
     return i0, t - i0
 
 
-def needle_field3d(n, seed, kappa=20.0, lattice=16):
+def needle_field3d(n, seed, kappa=20.0, lattice=16, dtype=np.float64):
     """3D SPD field with eigenvalues (1, kappa^-2, kappa^-2) and smooth random
     orientation: seeded random unit vectors v on a lattice^3 grid, the
     projector P = v v^T trilinearly interpolated entrywise, and
-    D = eps I + (1 - eps) P with eps = kappa^-2 (SPD, anisotropy <= kappa)."""
+    D = eps I + (1 - eps) P with eps = kappa^-2 (SPD, anisotropy <= kappa).
+    Returns the six planes (Dxx, Dyy, Dzz, Dxy, Dxz, Dyz), each (n, n, n),
+    computed one z plane at a time (FP64, then cast to dtype)."""
     g = rng(seed)
     v = g.normal(size=(lattice, lattice, lattice, 3))
     v /= np.linalg.norm(v, axis=-1, keepdims=True)
     P = v[..., :, None] * v[..., None, :]           # (L, L, L, 3, 3), index [z, y, x]
     iz, fz = _lattice_coords(n, lattice)
-    out = np.zeros((n, n, n, 3, 3))
-    for dz in (0, 1):
-        wz = (fz if dz else 1 - fz)[:, None, None, None, None]
-        for dy in (0, 1):
-            wy = (fz if dy else 1 - fz)[None, :, None, None, None]
-            for dx in (0, 1):
-                wx = (fz if dx else 1 - fz)[None, None, :, None, None]
-                blk = P[iz + dz][:, iz + dy][:, :, iz + dx]
-                out += wz * wy * wx * blk
     eps = 1.0 / kappa ** 2
-    D = eps * np.eye(3) + (1 - eps) * out
-    return np.stack([D[..., 0, 0], D[..., 1, 1], D[..., 2, 2], D[..., 0, 1], D[..., 0, 2],
-                     D[..., 1, 2]])
+    res = np.empty((6, n, n, n), dtype=dtype)
+    for z in range(n):
+        out = np.zeros((n, n, 3, 3))
+        for dz in (0, 1):
+            wz = fz[z] if dz else 1 - fz[z]
+            for dy in (0, 1):
+                wy = (fz if dy else 1 - fz)[:, None, None, None]
+                for dx in (0, 1):
+                    wx = (fz if dx else 1 - fz)[None, :, None, None]
+                    blk = P[iz[z] + dz][iz + dy][:, iz + dx]
+                    out += wz * wy * wx * blk
+        D = eps * np.eye(3) + (1 - eps) * out
+        for k, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+            res[k, z] = D[..., a, b]
+    return res
 
 
 def smooth_field2d(ny, nx, seed, kappa_min=1.0, kappa_max=50.0, lattice=16):

@@ -140,3 +140,25 @@ def test_apply_full_size_4096():
     ref = oracle.apply((n, n), oracle.NEUMANN, oo, ow, useen)
     assert np.abs(Au - ref).max() <= 1e-5 * np.abs(ref).max()
     assert abs(Au.sum()) <= 1e-6 * np.abs(Au).sum()
+
+
+@pytest.mark.parametrize("bc", [ab.NEUMANN, ab.PERIODIC])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_max_diag_matches_oracle(bc, dim):
+    """max_z A_zz (the explicit limit dt = 1 / max A_zz) against the oracle's
+    diagonal; FP32 accumulation on the device."""
+    t = torch()
+    if dim == 2:
+        shape = (45, 67)
+        D = synth.smooth_field2d(*shape, seed=3, kappa_min=1, kappa_max=60, lattice=6)
+    else:
+        shape = (13, 17, 19)
+        D = synth.needle_field3d(19, seed=5, kappa=15.0)[:, :13, :17, :19]
+    h, seen, _ = build(D, shape, t.float32, ab.F32, bc)
+    try:
+        m = ab.adlbr_stencils_max_diag(h)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    oo, ow = _oracle_stencils(seen, dim)
+    ref = oracle.diag(shape, bc, oo, ow).max()
+    assert abs(m - ref) <= 1e-5 * ref, (m, ref)

@@ -140,3 +140,29 @@ def test_trained_preconditioner_report():
           % (it_cg, its["jacobi"][0], its["trained"][0]))
     for name, (it, rel, d) in its.items():
         assert rel <= 1e-4 and d <= 2e-4, (name, it, rel, d)
+
+
+def test_bad_network_falls_back_to_cg():
+    """An untrained network with a large output layer spoils the flexible
+    solve; the solver detects it and finishes with plain CG at the same
+    residual (iterations then count both phases)."""
+    t = torch()
+    shape = (96, 112)
+    h, oo, ow, diag, dt = _problem(shape, 3)
+    theta = _params(4, scale_out=50.0)
+    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0])
+    try:
+        b = dev(synth.u_uniform(shape, 3).ravel(), t.float32)
+        x1 = b.clone()
+        it_cg, _ = ab.adlbr_step_implicit(h, b, x1, dt, 1e-6, 4000)
+        x2 = b.clone()
+        it_nn, rel = ab.adlbr_step_implicit(h, b, x2, dt, 1e-6, 4000, precond=1, nn=pc.desc)
+        fb = ab.adlbr_last_fallback()
+        d = (x1 - x2).abs().max().item()
+    finally:
+        pc.close()
+        ab.adlbr_stencils_destroy(h)
+    print("CG %d, bad-network solve %d (fallback %d)" % (it_cg, it_nn, fb))
+    assert fb == 1
+    assert it_nn > it_cg
+    assert rel <= 1e-5 and d <= 2e-4, (rel, d)
