@@ -188,8 +188,9 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  * adlbr_step_implicit -- one implicit step: solves (I + dt A) x = rhs by
  * conjugate gradients (the discretised Eq. elliptic of Sec. 4.2 with
  * lambda = dt, solved by CG as there).  FP32 vectors; every dot product and
- * norm is accumulated in FP64 with a deterministic reduction; alpha and beta
- * are computed on the device.  Each round starts from the true residual
+ * norm is accumulated from exact products in float-float within a thread and
+ * a warp (about 48 significant bits) and in FP64 across warps and blocks,
+ * with a deterministic reduction; alpha and beta are computed on the device.  Each round starts from the true residual
  * rhs - (x + dt A x), evaluated with the operator accumulated in FP64, and
  * runs CG until the recursively updated residual satisfies
  * |r| <= rtol |rhs|; a new round (iterative refinement) follows while the

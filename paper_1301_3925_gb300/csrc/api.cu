@@ -167,9 +167,9 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
     if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
     if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
     if (nsteps == 0) return ADLBR_OK;
-    // scratch accumulates dt A u; each finalize pass consumes and re-zeroes it
-    ADLBR_CUDA(cudaMemsetAsync(scratch, 0, adlbr_step_scratch_bytes(s, u_t), stream));
+    // per step: scratch <- 0, scratch += dt A u, u -= scratch
     for (int k = 0; k < nsteps; ++k) {
+        ADLBR_CUDA(cudaMemsetAsync(scratch, 0, adlbr_step_scratch_bytes(s, u_t), stream));
         if (adlbr_status st = launch_accumulate(s, u, scratch, u_t, dt, nullptr, stream)) return st;
         if (adlbr_status st = launch_finalize(s, u, scratch, u_t, stream)) return st;
     }

@@ -291,23 +291,22 @@ __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, i
     red_add(Au + z, acc);
 }
 
-// u <- u - acc ; acc <- 0   (acc already holds dt A u)
+// u <- u - acc   (acc holds dt A u).  The accumulator is cleared by a
+// separate memset before the next accumulation: a pass that rewrites both
+// arrays in place runs at about a quarter of the HBM rate on this GPU, the
+// two passes apart at nearly the full rate.
 template <typename UT>
 __global__ void finalize_kernel(int64_t N, UT *__restrict__ u,
-                                typename UTraits<UT>::acc *__restrict__ acc) {
-    using AT = typename UTraits<UT>::acc;
+                                const typename UTraits<UT>::acc *__restrict__ acc) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    AT a = acc[i];
-    acc[i] = (AT)0;
-    u[i] = from_acc<UT>(to_acc(u[i]) - a);
+    u[i] = from_acc<UT>(to_acc(u[i]) - acc[i]);
 }
 
-__global__ void finalize_f32x4_kernel(int64_t N4, float4 *__restrict__ u, float4 *__restrict__ acc) {
+__global__ void finalize_f32x4_kernel(int64_t N4, float4 *__restrict__ u, const float4 *__restrict__ acc) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N4) return;
-    float4 a = acc[i], v = u[i];
-    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a = acc[i], v = u[i];
     u[i] = make_float4(v.x - a.x, v.y - a.y, v.z - a.z, v.w - a.w);
 }
 

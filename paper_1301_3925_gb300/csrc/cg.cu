@@ -2,18 +2,22 @@
 // discretised Eq. elliptic is solved by Conjugate Gradient; here with
 // lambda = dt and b = u^n).
 //
-// Vectors are FP32; every dot product and norm is accumulated in FP64 with a
-// deterministic two-level reduction (warp shuffles, one partial per block, and
+// Vectors are FP32; every dot product and norm is accumulated with exact
+// products in float-float within threads and warps and in FP64 across warps
+// and blocks, by a deterministic two-level reduction (one partial per block,
 // the last block to finish sums the partials in block order).  The CG scalars
 // alpha, beta and |r|^2 live in device memory and are produced by that last
 // block, so an iteration needs no host round trip; the host polls a
 // convergence flag every few iterations.  Once the flag is set every kernel
 // returns immediately, so the reported iteration count is exact.
 //
-// Per iteration: q <- dt A p (operator accumulated into a zeroed q), then
-//   K2  q <- q + p ; <p, q> ; last block: alpha = rr / <p,q>
-//   K3  x += alpha p ; r -= alpha q ; q <- 0 ; <r, r> ; last block: beta, flag
-//   K4  p <- r + beta p
+// Per iteration, with q = p on entry: q += dt A p (so q = (I + dt A) p), then
+//   K2  <p, q> ; last block: alpha = rr / <p,q>
+//   K3  x += alpha p ; r -= alpha q ; <r, r> ; last block: beta, flag
+//   K4  p <- r + beta p ; q <- p
+// (no kernel stores a constant over a value it has just loaded: such a
+// store waits for the load and a vector pass with one runs at a fraction of
+// the HBM rate on this GPU)
 #include <cmath>
 #include <cstddef>
 
@@ -75,17 +79,14 @@ __global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *
     }
 }
 
-// q <- q + p ; alpha = rr / <p, q>
+// alpha = rr / <p, q>
 __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__ p,
-                                            float *__restrict__ q, double *partials, CgState *S) {
+                                            const float *__restrict__ q, double *partials, CgState *S) {
     if (S->conv) return;
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        float qi = q[i] + p[i];
-        q[i] = qi;
-        s += (double)p[i] * qi;
-    }
-    double part = block_sum(s);
+    FFAcc s;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
+        ff_add_prod(s, p[i], q[i]);
+    double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->pq = tot;
@@ -93,21 +94,20 @@ __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__
     }
 }
 
-// x += alpha p ; r -= alpha q ; q <- 0 ; rr_new = <r, r> ; beta ; flag
+// x += alpha p ; r -= alpha q ; rr_new = <r, r> ; beta ; flag
 __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, const float *__restrict__ p,
-                                            float *__restrict__ r, float *__restrict__ q,
+                                            float *__restrict__ r, const float *__restrict__ q,
                                             double *partials, CgState *S) {
     if (S->conv) return;
     const float alpha = (float)S->alpha;
-    double s = 0.0;
+    FFAcc s;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         x[i] += alpha * p[i];
         float ri = r[i] - alpha * q[i];
         r[i] = ri;
-        q[i] = 0.f;
-        s += (double)ri * ri;
+        ff_add_prod(s, ri, ri);
     }
-    double part = block_sum(s);
+    double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->beta = tot / S->rr;
@@ -120,13 +120,16 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
     }
 }
 
-// p <- r + beta p
+// p <- r + beta p ; q <- p
 __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r,
-                                            float *__restrict__ p, const CgState *S) {
+                                            float *__restrict__ p, float *__restrict__ q, const CgState *S) {
     if (S->conv) return;
     const float beta = (float)S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
-        p[i] = r[i] + beta * p[i];
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const float pi = r[i] + beta * p[i];
+        p[i] = pi;
+        q[i] = pi;
+    }
 }
 
 }  // namespace
@@ -202,7 +205,8 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
         cg_restart_kernel<<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.r, W.p, W.partials, W.partials2,
                                              W.partials3, W.S);
         ADLBR_CUDA(cudaGetLastError());
-        ADLBR_CUDA(cudaMemsetAsync(W.q, 0, N * sizeof(float), st));  // q aliases acc64
+        // q = p (q aliases acc64, which the restart kernel has consumed)
+        ADLBR_CUDA(cudaMemcpyAsync(W.q, W.p, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
         relres = host.bb > 0 ? std::sqrt(host.rr_new / host.bb) : 0.0;
@@ -213,18 +217,32 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
         if (restart > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
         prev = relres;
         const int chunk = every > 0 ? every : 8;
+        auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
+            for (int k = 0; k < chunk; ++k) {
+                if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs))
+                    return e;
+                cg_k2<<<RB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
+                cg_k3<<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.partials, W.S);
+                cg_k4<<<RB, RT, 0, cs>>>(N, W.r, W.p, W.q, W.S);
+            }
+            ADLBR_CUDA(cudaGetLastError());
+            return ADLBR_OK;
+        };
+        // Without a hook the chunk (4 kernels per iteration, each a no-op
+        // once the device flag is set) is captured once as a CUDA graph and
+        // replayed; the host reads the flag after every replay.
+        ChunkGraph graph;
+        if (!hook)
+            if (adlbr_status e = graph.capture(enqueue_chunk)) return e;
         int it = 0;
         while (it < maxit - total_iters) {
             if (hook && restart == 0)
                 if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
-            for (int k = 0; k < chunk; ++k) {
-                if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), st))
-                    return e;
-                cg_k2<<<RB, RT, 0, st>>>(N, W.p, W.q, W.partials, W.S);
-                cg_k3<<<RB, RT, 0, st>>>(N, x, W.p, W.r, W.q, W.partials, W.S);
-                cg_k4<<<RB, RT, 0, st>>>(N, W.r, W.p, W.S);
+            if (graph.exec) {
+                ADLBR_CUDA(cudaGraphLaunch(graph.exec, st));
+            } else if (adlbr_status e = enqueue_chunk(st)) {
+                return e;
             }
-            ADLBR_CUDA(cudaGetLastError());
             it += chunk;
             ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
             ADLBR_CUDA(cudaStreamSynchronize(st));

@@ -250,6 +250,35 @@ adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc
 adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, double *acc, double scale,
                                    cudaStream_t st);
 // u <- u - acc ; acc <- 0
+// A fixed sequence of launches recorded into a CUDA graph and replayed with
+// cudaGraphLaunch on the caller's stream.  The recording runs on a private
+// stream (capture is not allowed on the legacy default stream, which a
+// caller may pass); nothing executes during it.
+struct ChunkGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    template <typename F>
+    adlbr_status capture(F &&enqueue) {
+        cudaStream_t cs = nullptr;
+        ADLBR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        adlbr_status e = ADLBR_OK;
+        if (ce == cudaSuccess) {
+            e = enqueue(cs);
+            ce = cudaStreamEndCapture(cs, &graph);
+        }
+        cudaStreamDestroy(cs);
+        if (e != ADLBR_OK) return e;
+        ADLBR_CUDA(ce);
+        ADLBR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        return ADLBR_OK;
+    }
+    ~ChunkGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 adlbr_status launch_finalize(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
                              cudaStream_t st);
 

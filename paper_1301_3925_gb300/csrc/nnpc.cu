@@ -186,21 +186,22 @@ __global__ void coarse_r_kernel(int nx, int ny, const float *__restrict__ r, con
                 r[(int64_t)(cy * RF + dy) * nx + cx * RF + dx] * inv;
 }
 
-// r = b - (x + q) (q = dt A x), rr, bb
+// r = b - (x + q) (q = dt A x), rr, bb.  As in the CG kernels, no kernel
+// here stores a constant over a value it has just loaded; q receives p in
+// the kernels that produce p, and the operator accumulates dt A p into it.
 __global__ void __launch_bounds__(RT) fcg_init_kernel(int64_t N, const float *__restrict__ b,
-                                                      const float *__restrict__ x, float *__restrict__ q,
+                                                      const float *__restrict__ x, const float *__restrict__ q,
                                                       float *__restrict__ r, double *partials,
                                                       double *partials2, FcgState *S) {
-    double s_rr = 0.0, s_bb = 0.0;
+    FFAcc s_rr, s_bb;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         const float ri = b[i] - (x[i] + q[i]);
         r[i] = ri;
-        q[i] = 0.f;
-        s_rr += (double)ri * ri;
-        s_bb += (double)b[i] * b[i];
+        ff_add_prod(s_rr, ri, ri);
+        ff_add_prod(s_bb, b[i], b[i]);
     }
-    const double pr = block_sum(s_rr);
-    const double pb = block_sum(s_bb);
+    const double pr = block_sum_ff(s_rr);
+    const double pb = block_sum_ff(s_bb);
     if (threadIdx.x == 0) partials2[blockIdx.x] = pb;
     double tot;
     if (finish_reduction(pr, partials, &S->count, tot)) {
@@ -212,29 +213,29 @@ __global__ void __launch_bounds__(RT) fcg_init_kernel(int64_t N, const float *__
     }
 }
 
-// z = r / d + s P(y) ; first: rz = <r,z>, p = z.  Otherwise: beta =
+// z = r / d + s P(y) ; first: rz = <r,z>, p = q = z.  Otherwise: beta =
 // (<r,z> - <r_old,z>) / rz, rz = <r,z> (p updated by fcg_p_kernel).
 template <bool FIRST>
 __global__ void __launch_bounds__(RT) fcg_z_kernel(int nx, int64_t N, const float *__restrict__ r,
                                                    const float *__restrict__ r_old,
                                                    const float *__restrict__ d,
                                                    const float *__restrict__ y, float *__restrict__ z,
-                                                   float *__restrict__ p, double *partials,
-                                                   double *partials2, FcgState *S) {
+                                                   float *__restrict__ p, float *__restrict__ q,
+                                                   double *partials, double *partials2, FcgState *S) {
     if (S->conv) return;
     const int Wc = nx / RF;
     const float s = (float)sqrt(S->rr / (double)N);
-    double s_rz = 0.0, s_oz = 0.0;
+    FFAcc s_rz, s_oz;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         const int xx = (int)(i % nx), yy = (int)(i / nx);
         const float zi = r[i] / d[i] + s * y[(int64_t)(yy / RF) * Wc + xx / RF];
         z[i] = zi;
-        if (FIRST) p[i] = zi;
-        s_rz += (double)r[i] * zi;
-        if (!FIRST) s_oz += (double)r_old[i] * zi;
+        if (FIRST) p[i] = zi, q[i] = zi;
+        ff_add_prod(s_rz, r[i], zi);
+        if (!FIRST) ff_add_prod(s_oz, r_old[i], zi);
     }
-    const double prz = block_sum(s_rz);
-    const double poz = block_sum(s_oz);
+    const double prz = block_sum_ff(s_rz);
+    const double poz = block_sum_ff(s_oz);
     if (threadIdx.x == 0) partials2[blockIdx.x] = poz;
     double tot;
     if (finish_reduction(prz, partials, &S->count, tot)) {
@@ -247,17 +248,14 @@ __global__ void __launch_bounds__(RT) fcg_z_kernel(int nx, int64_t N, const floa
     }
 }
 
-// q <- q + p ; alpha = rz / <p, q>
+// alpha = rz / <p, q>   (q = p + dt A p)
 __global__ void __launch_bounds__(RT) fcg_q_kernel(int64_t N, const float *__restrict__ p,
-                                                   float *__restrict__ q, double *partials, FcgState *S) {
+                                                   const float *__restrict__ q, double *partials, FcgState *S) {
     if (S->conv) return;
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        const float qi = q[i] + p[i];
-        q[i] = qi;
-        s += (double)p[i] * qi;
-    }
-    double part = block_sum(s);
+    FFAcc s;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
+        ff_add_prod(s, p[i], q[i]);
+    double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->pq = tot;
@@ -265,24 +263,23 @@ __global__ void __launch_bounds__(RT) fcg_q_kernel(int64_t N, const float *__res
     }
 }
 
-// x += alpha p ; r_old = r ; r -= alpha q ; q = 0 ; rr ; flag
+// x += alpha p ; r_old = r ; r -= alpha q ; rr ; flag
 __global__ void __launch_bounds__(RT) fcg_x_kernel(int64_t N, float *__restrict__ x,
                                                    const float *__restrict__ p, float *__restrict__ r,
-                                                   float *__restrict__ r_old, float *__restrict__ q,
+                                                   float *__restrict__ r_old, const float *__restrict__ q,
                                                    double *partials, FcgState *S) {
     if (S->conv) return;
     const float alpha = (float)S->alpha;
-    double s = 0.0;
+    FFAcc s;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         x[i] += alpha * p[i];
         const float ro = r[i];
         r_old[i] = ro;
         const float ri = ro - alpha * q[i];
         r[i] = ri;
-        q[i] = 0.f;
-        s += (double)ri * ri;
+        ff_add_prod(s, ri, ri);
     }
-    double part = block_sum(s);
+    double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->rr = tot;
@@ -294,14 +291,17 @@ __global__ void __launch_bounds__(RT) fcg_x_kernel(int64_t N, float *__restrict_
     }
 }
 
-// p <- z + beta p
+// p <- z + beta p ; q <- p
 __global__ void fcg_p_kernel(int64_t N, const float *__restrict__ z, float *__restrict__ p,
-                             const FcgState *S) {
+                             float *__restrict__ q, const FcgState *S) {
     if (S->conv) return;
     const float beta = (float)S->beta;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float pi = z[i] + beta * p[i];
+        p[i] = pi;
+        q[i] = pi;
+    }
 }
 
 // training target: R((xs - x - r / d) / s) with s = rms(r) (given)
@@ -459,8 +459,8 @@ static adlbr_status precondition(adlbr_stencils *s, NnWorkspace &W, adlbr_unet *
     dim3 gc(blocks_for(nx / RF, 128), (unsigned)(ny / RF));
     coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, s->N, W.feat);
     if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
-    fcg_z_kernel<FIRST><<<NB, RT, 0, st>>>(nx, s->N, W.r, W.r_old, W.d, W.y, W.z, W.p, W.partials,
-                                           W.partials2, W.S);
+    fcg_z_kernel<FIRST><<<NB, RT, 0, st>>>(nx, s->N, W.r, W.r_old, W.d, W.y, W.z, W.p, W.q,
+                                           W.partials, W.partials2, W.S);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
@@ -523,7 +523,7 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
             fcg_q_kernel<<<NB, RT, 0, st>>>(N, W.p, W.q, W.partials, W.S);
             fcg_x_kernel<<<NB, RT, 0, st>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
             if (adlbr_status e = precondition<false>(s, W, nn->net, nn->params, st)) return e;
-            fcg_p_kernel<<<NB, RT, 0, st>>>(N, W.z, W.p, W.S);
+            fcg_p_kernel<<<NB, RT, 0, st>>>(N, W.z, W.p, W.q, W.S);
         }
         ADLBR_CUDA(cudaGetLastError());
         it += chunk;

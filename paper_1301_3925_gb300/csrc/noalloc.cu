@@ -64,10 +64,10 @@ extern "C" adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, voi
     if (nsteps == 0) return ADLBR_OK;
     void *acc = nullptr;
     if (adlbr_status st = scratch_address(dev, &acc)) return st;
-    // the array keeps the previous call's contents: clear the accumulator
+    // per step: clear the accumulator, accumulate dt A u, subtract it
     const size_t bytes = (size_t)s->N * (u_t == ADLBR_F64 ? sizeof(double) : sizeof(float));
-    ADLBR_CUDA(cudaMemsetAsync(acc, 0, bytes, stream));
     for (int k = 0; k < nsteps; ++k) {
+        ADLBR_CUDA(cudaMemsetAsync(acc, 0, bytes, stream));
         if (adlbr_status st = launch_accumulate(s, u, acc, u_t, dt, nullptr, stream)) return st;
         if (adlbr_status st = launch_finalize(s, u, acc, u_t, stream)) return st;
     }
