@@ -36,7 +36,9 @@ CED = dict(sigma=1.0, rho=4.0, alpha=1e-4, C=1e-5, dt=0.02)
 SEED = 1
 # DRAM bytes (read + write) of one launch at 4096^2, from ncu captures of the
 # current kernels (the summaries under profiles/ give the commands)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.17e6 + 140.37e6, "build2d_kernel": 201.50e6 + 229.51e6}
+TRAFFIC_4096 = {"ced_fused_kernel": 67.16e6 + 140.92e6, "build2d_kernel": 201.44e6 + 229.27e6,
+                # operator + finalize
+                "explicit_step": 402.76e6 + 51.59e6 + 134.22e6 + 21.37e6}
 
 
 def parse():
@@ -50,6 +52,8 @@ def parse():
     p.add_argument("--no-implicit", action="store_true", help="skip the implicit-step measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D measurement and precision study")
     p.add_argument("--precision-steps", type=int, default=100)
+    p.add_argument("--profile-cg", action="store_true",
+                   help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
     return p.parse_args()
 
 
@@ -214,6 +218,30 @@ def implicit_measurement(peak):
         ab.adlbr_stencils_destroy(h)
 
 
+def profile_cg():
+    """Three plain-CG solves of the 2048^2 implicit step (profiling entry)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    n = 2048
+    D = torch.from_numpy(synth.smooth_field2d(n, n, 3, 1.0, 50.0, 16).reshape(3, -1)
+                         .astype(np.float32)).cuda()
+    g = ab.grid((n, n))
+    h = ab.adlbr_build_stencils(g, D, ab.F32, ab.F32)
+    dt = 200.0 / ab.adlbr_stencils_max_diag(h)
+    b = torch.from_numpy(synth.u_uniform((n, n), 3).astype(np.float32).ravel()).cuda()
+    x = torch.empty_like(b)
+    for _ in range(3):
+        x.copy_(b)
+        it, rel = ab.adlbr_step_implicit(h, b, x, dt, 1e-6, 4000)
+    torch.cuda.synchronize()
+    ab.adlbr_stencils_destroy(h)
+    print(json.dumps({"profile_cg": {"iters": it, "relres": rel}}))
+    return 0
+
+
 def volume_measurement(peak, steps):
     """3D 256^3 needle field (eigenvalues 1, 1/400, 1/400, smooth random
     orientation on a 16^3 lattice, seed 2): stencil build, operator and
@@ -344,6 +372,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     import torch
+    if args.profile_cg:
+        return profile_cg()
 
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
