@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-implicit", action="store_true", help="skip the implicit-step measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D measurement and precision study")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-step measurement")
     p.add_argument("--precision-steps", type=int, default=100)
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
@@ -240,6 +241,69 @@ def profile_cg():
     ab.adlbr_stencils_destroy(h)
     print(json.dumps({"profile_cg": {"iters": it, "relres": rel}}))
     return 0
+
+
+def batch_measurement(peak, steps=20):
+    """Serving-style batch: 64 images (sides U{256..2048}) and 8 volumes
+    (sides U{64..192}), each with its own seeded field (kappa_i ~ U[5, 100]:
+    smooth 2D orientation field / 3D needle field), F16 weights, FP32 u,
+    dt_i = 1 / max A_zz.  `steps` batched steps (one graph launch each,
+    autotuned tile shapes) against the same steps issued item by item."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    items = synth.batch_items()
+    st = torch.cuda.current_stream()
+    hs, us, dts = [], [], []
+    pts2, pts3 = 0, 0
+    try:
+        for k, it in enumerate(items):
+            shape = it["shape"]
+            if it["dim"] == 2:
+                D = synth.smooth_field2d_torch(*shape, it["seed"], 1.0, it["kappa"], 16).reshape(3, -1)
+                pts2 += shape[0] * shape[1]
+            else:
+                D = torch.from_numpy(synth.needle_field3d(shape[0], it["seed"], kappa=it["kappa"],
+                                                          dtype=np.float32).reshape(6, -1)).cuda()
+                pts3 += shape[0] ** 3
+            h = ab.adlbr_build_stencils(ab.grid(shape), D, ab.F32, ab.F16)
+            hs.append(h)
+            del D
+            dts.append(1.0 / ab.adlbr_stencils_max_diag(h))
+            us.append(torch.rand(int(np.prod(shape)), device="cuda",
+                                 generator=torch.Generator(device="cuda").manual_seed(it["seed"])))
+        t0 = time.perf_counter()
+        b = ab.adlbr_batch_create(hs, us, dts, autotune=True)
+        tune_s = time.perf_counter() - t0
+        try:
+            shape, tuned_ms, points, ntiles = ab.adlbr_batch_config(b)
+            ab.adlbr_batch_step(b, 2)
+            ms = time_ms(lambda: ab.adlbr_batch_step(b, steps), 1, st) / steps
+        finally:
+            ab.adlbr_batch_destroy(b)
+        scratch = [torch.empty(ab.adlbr_step_scratch_bytes(h, ab.F32), dtype=torch.uint8, device="cuda")
+                   for h in hs]
+
+        def looped():
+            for _ in range(steps):
+                for h, u, d, sc in zip(hs, us, dts, scratch):
+                    ab.adlbr_step_explicit(h, u, sc, ab.F32, d, 1)
+
+        ms_loop = time_ms(looped, 1, st) / steps
+        algo = 24 * pts2 + 36 * pts3
+        gbs = algo / (ms * 1e-3) / 1e9
+        return {"items": {"images": sum(1 for i in items if i["dim"] == 2),
+                          "volumes": sum(1 for i in items if i["dim"] == 3)},
+                "points": points, "steps": steps, "tiles": ntiles,
+                "shape": {"tile2d": list(shape[:2]), "block3d": list(shape[2:])},
+                "create_s": tune_s, "tuned_accumulate_ms": tuned_ms,
+                "ms_per_step": ms, "gpts": points / (ms * 1e-3) / 1e9, "gbs": gbs,
+                "frac_hbm": gbs / peak, "bytes_per_point": {"2d": 24, "3d": 36},
+                "looped_ms_per_step": ms_loop, "speedup_vs_looped": ms_loop / ms,
+                "kernel_launches_per_step": {"batched": 2, "looped": 2 * len(hs)}}
+    finally:
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
 
 
 def volume_measurement(peak, steps):
@@ -502,6 +566,7 @@ def main():
 
     implicit = None if args.no_implicit or rank != 0 else implicit_measurement(peak)
     volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)
+    batch = None if args.no_batch or rank != 0 else batch_measurement(peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -520,7 +585,7 @@ def main():
                 "stages_ms": {"tensor": st_tensor, "build": st_build, "explicit_step": st_step},
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
-                "apply": apply_sub, "implicit": implicit, "volume3d": volume}
+                "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:

@@ -352,6 +352,44 @@ adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, v
                             double sigma, double rho, double alpha, double C, double dt,
                             int nsteps, adlbr_dtype w_t, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched explicit steps (not in the paper: its explicit scheme of Sec. 4.4,
+ * u <- u - dt_i A_i u_i, applied to many images and volumes of uneven sizes
+ * at once).
+ * ------------------------------------------------------------------------ */
+typedef struct adlbr_batch adlbr_batch; /* opaque: items, work list, accumulator, graph */
+
+/*
+ * adlbr_batch_create -- fixes a batch of n_items items: the stencil handles
+ * s[i] (2D or 3D, any weight type, built beforehand and kept alive by the
+ * caller), the FP32 u buffers u[i] (device, N_i floats each, updated in
+ * place by adlbr_batch_step) and the time steps dt[i] >= 0.
+ * It allocates one accumulator for all items and a work list of tiles (2D
+ * tiles of the shared-window operator, 3D blocks of the scatter operator).
+ * With autotune != 0 it times the accumulate kernel of every candidate tile
+ * shape on this batch (u is not modified) and keeps the fastest, else the
+ * first candidate (64 x 32 tiles, 32 x 8 x 4 blocks).  One step (accumulator
+ * reset, one persistent accumulate kernel over all tiles of all items with
+ * dynamic tile hand-out, one finalize kernel) is recorded as a CUDA graph.
+ * Synchronises the stream.  The handles' stencils must not be rebuilt with a
+ * different shape while the batch lives (rebuilding in place is fine).
+ */
+adlbr_status adlbr_batch_create(int n_items, adlbr_stencils *const *s, float *const *u,
+                                const double *dt, int autotune, adlbr_batch **out,
+                                cudaStream_t stream);
+
+/* nsteps explicit steps of every item: nsteps launches of the recorded
+ * graph on `stream`. */
+adlbr_status adlbr_batch_step(adlbr_batch *b, int nsteps, cudaStream_t stream);
+
+/* The chosen shape (shape_out[5] = 2D tile width, height, 3D block x, y,
+ * planes per thread), the tuned accumulate time in ms (0 without tuning),
+ * the total number of points and of tiles.  Any pointer may be NULL. */
+adlbr_status adlbr_batch_config(const adlbr_batch *b, int *shape_out, double *tuned_ms,
+                                int64_t *points, int *n_tiles);
+
+adlbr_status adlbr_batch_destroy(adlbr_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

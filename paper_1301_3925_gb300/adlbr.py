@@ -68,6 +68,11 @@ def lib():
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
             "adlbr_last_fallback": (_i32, []),
+            "adlbr_batch_create": (_i32, [_i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp), _vp]),
+            "adlbr_batch_step": (_i32, [_vp, _i32, _vp]),
+            "adlbr_batch_config": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_i32)]),
+            "adlbr_batch_destroy": (_i32, [_vp]),
             "adlbr_unet_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32,
                                          ctypes.POINTER(_vp)]),
             "adlbr_unet_destroy": (_i32, [_vp]),
@@ -293,3 +298,34 @@ def adlbr_step_implicit(h, rhs, x, dt, rtol, maxit, precond=0, nn=None, stream=N
 def adlbr_last_fallback():
     """1 if the last preconditioned implicit solve of this thread fell back to plain CG."""
     return int(lib().adlbr_last_fallback())
+
+
+def adlbr_batch_create(handles, us, dts, autotune=True, stream=None):
+    """Batch of explicit steps over items (handle, FP32 u tensor, dt); returns the batch address."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*handles)
+    U = (ctypes.c_void_p * n)(*[_ptr(x) for x in us])
+    T = (ctypes.c_double * n)(*[float(d) for d in dts])
+    out = ctypes.c_void_p()
+    _check(lib().adlbr_batch_create(n, ctypes.cast(H, ctypes.c_void_p), ctypes.cast(U, ctypes.c_void_p),
+                                    ctypes.cast(T, ctypes.c_void_p), 1 if autotune else 0,
+                                    ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def adlbr_batch_step(b, nsteps, stream=None):
+    _check(lib().adlbr_batch_step(b, int(nsteps), _stream(stream)))
+
+
+def adlbr_batch_config(b):
+    """(shape (tw, th, bx, by, bz), tuned ms, points, tiles)."""
+    sh = (_i32 * 5)()
+    ms = ctypes.c_double(0.0)
+    pts = ctypes.c_int64(0)
+    nt = _i32(0)
+    _check(lib().adlbr_batch_config(b, sh, ctypes.byref(ms), ctypes.byref(pts), ctypes.byref(nt)))
+    return tuple(sh), ms.value, pts.value, nt.value
+
+
+def adlbr_batch_destroy(b):
+    _check(lib().adlbr_batch_destroy(b))

@@ -11,76 +11,16 @@
 // tiled kernel below; 95% of the edges of the kappa <= 100 CED stencils are
 // at most 8 points long).  The FP64 path and the 3D path push every
 // contribution to L2 directly.
-#include <type_traits>
-
-#include "internal.cuh"
+#include "operator.cuh"
 
 namespace adlbr {
 
 namespace {
 
-__device__ __forceinline__ int wrap(int c, int n) {
-    c %= n;
-    return c < 0 ? c + n : c;
-}
-
-__device__ __forceinline__ void red_add(float *p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-                 "f"(d)
-                 : "memory");
-}
-
-// ---- 2D, shared-memory window ------------------------------------------
-// A CTA owns a TW x TH tile.  It stages u over the tile plus an 8-point halo
-// in shared memory, and keeps a shared accumulator over the same window.  An
-// edge whose offset has Chebyshev length <= HALO stays inside the window for
-// every point of the tile, so its neighbour value and both of its pushes are
-// shared-memory operations; in a tile whose window lies inside the grid (or
-// on a periodic grid) such edges need no boundary test either.  Longer edges
-// read u from global memory and push to L2.  The window is then flushed with
-// 16-byte vector reductions.
-constexpr int HALO = 8;
-
-// A warp covers WX x (32 / WX) points of the tile per pass; the row pitch P
-// of the shared window puts the rows of one warp on disjoint bank ranges, so
-// lanes that share an offset hit 32 different banks.
-constexpr int window_pitch(int ww, int wx) {
-    for (int p = ww;; p += 4) {
-        bool ok = true;
-        for (int r = 1; r < 32 / wx; ++r) {
-            const int b = (r * p) % 32;
-            if (b < wx || b > 32 - wx) ok = false;
-        }
-        if (ok) return p;
-    }
-}
-
-template <int TW, int TH, int NT, int WX>
-struct Tile {
-    static constexpr int WW = TW + 2 * HALO, WH = TH + 2 * HALO;
-    static constexpr int WR = 32 / WX;                   // rows per warp pass
-    static constexpr int WARPS_X = TW / WX, WARPS_Y = NT / 32 / WARPS_X;
-    static constexpr int P = window_pitch(WW, WX);       // shared row pitch (floats)
-    static constexpr int PASSES = TH / (WR * WARPS_Y);
-    static_assert(TW % WX == 0 && (NT / 32) % WARPS_X == 0 && TH % (WR * WARPS_Y) == 0, "tile");
-    static_assert(WW % 4 == 0 && P % 4 == 0, "window rows must hold whole float4s");
-};
-
-// Weights of point z times `scale`.  For the F16 format the half is widened
-// by moving its bits to the FP32 position and multiplying by 2^112 (exact,
-// subnormal halves included); the per-point power of two and `scale` are
-// applied by one more product, as in load_weights.
-__device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z, float scale,
-                                                   float (&w)[3]) {
-    const uint2 r = reinterpret_cast<const uint2 *>(wbase)[z];
-    const int s = (int)(int8_t)(r.y >> 24);
-    const float c = __int_as_float((127 + s) << 23) * scale;
-    w[0] = __uint_as_float((r.x & 0xffffu) << 13) * 0x1p112f * c;
-    w[1] = __uint_as_float((r.x >> 16) << 13) * 0x1p112f * c;
-    w[2] = __uint_as_float((r.y & 0xffffu) << 13) * 0x1p112f * c;
-}
+using op::HALO;
+using op::red_add;
+using op::Tile;
+using op::wrap;
 
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W>
 __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, float scale,
@@ -88,129 +28,10 @@ __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, floa
                                                     const void *__restrict__ wbase, adlbr_dtype wt,
                                                     const UT *__restrict__ u, float *__restrict__ acc,
                                                     const int *__restrict__ skip) {
-    using T = Tile<TW, TH, NT, WX>;
-    constexpr int WW = T::WW, WH = T::WH, P = T::P;
     extern __shared__ __align__(16) float smem[];
-    float *uw = smem, *aw = smem + WH * P;
     if (skip && *skip) return;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
-    const bool periodic = bc == ADLBR_PERIODIC;
-    // full: every point of the tile is in the grid; inside: every short edge
-    // of the tile stays in the grid (or wraps, on a periodic grid)
-    const bool full = x0 + TW <= nx && y0 + TH <= ny;
-    const bool inside = periodic || (x0 >= HALO && y0 >= HALO && x0 + TW + HALO <= nx &&
-                                     y0 + TH + HALO <= ny);
-    // stage u over the window (4 cells per step), zero the accumulator
-    const bool vec = std::is_same<UT, float>::value && (nx % 4) == 0 && !periodic &&
-                     ((uintptr_t)u % 16) == 0;
-    for (int c4 = threadIdx.x; c4 < WH * WW / 4; c4 += NT) {
-        const int wy = c4 / (WW / 4), wx = (c4 % (WW / 4)) * 4;
-        const int gy = y0 - HALO + wy, gx = x0 - HALO + wx;
-        float v[4];
-        if (vec && (unsigned)gy < (unsigned)ny && gx >= 0 && gx + 3 < nx) {
-            const float4 q = *reinterpret_cast<const float4 *>(
-                reinterpret_cast<const float *>(u) + (int64_t)gy * nx + gx);
-            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-        } else {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                int xx = gx + t, yy = gy;
-                v[t] = 0.f;
-                if (periodic) {
-                    xx = wrap(xx, nx);
-                    yy = wrap(yy, ny);
-                } else if ((unsigned)xx >= (unsigned)nx || (unsigned)yy >= (unsigned)ny) {
-                    continue;
-                }
-                v[t] = to_acc(u[(int64_t)yy * nx + xx]);
-            }
-        }
-        *reinterpret_cast<float4 *>(&uw[wy * P + wx]) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(&aw[wy * P + wx]) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tx = (warp % T::WARPS_X) * WX + lane % WX;
-    const int ty = (warp / T::WARPS_X) * T::WR + lane / WX;
-    const int x = x0 + tx;
-#pragma unroll 2
-    for (int k = 0; k < T::PASSES; ++k) {
-        const int ly = ty + k * T::WR * T::WARPS_Y, y = y0 + ly;
-        if (!full && (x >= nx || y >= ny)) continue;
-        const int64_t z = (int64_t)y * nx + x;
-        const short4 o = offs[z];
-        float w[3];
-        if (F16W) {
-            weights_f16_scaled(wbase, z, scale, w);
-        } else {
-            load_weights<float, 3>(wbase, wt, z, w);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) w[i] *= scale;
-        }
-        const int ex[3] = {o.x, o.z, -o.x - o.z}, ey[3] = {o.y, o.w, -o.y - o.w};
-        const int zw = (ly + HALO) * P + tx + HALO;
-        const float uz = uw[zw];
-        float own = 0.f;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float wi = w[i];
-            if (abs(ex[i]) <= HALO && abs(ey[i]) <= HALO) {
-                const int d = ey[i] * P + ex[i];
-#pragma unroll
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    if (!inside) {
-                        const int xn = x + sg * ex[i], yn = y + sg * ey[i];
-                        if ((unsigned)xn >= (unsigned)nx || (unsigned)yn >= (unsigned)ny) continue;
-                    }
-                    const int zn = zw + sg * d;
-                    const float f = wi * (uz - uw[zn]);
-                    own += f;
-                    atomicAdd(&aw[zn], -f);
-                }
-            } else if (wi != 0.f) {
-#pragma unroll
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    int xn = x + sg * ex[i], yn = y + sg * ey[i];
-                    if (periodic) {
-                        xn = wrap(xn, nx);
-                        yn = wrap(yn, ny);
-                    } else if ((unsigned)xn >= (unsigned)nx || (unsigned)yn >= (unsigned)ny) {
-                        continue;
-                    }
-                    const int64_t zn = (int64_t)yn * nx + xn;
-                    const float f = wi * (uz - to_acc(u[zn]));
-                    own += f;
-                    red_add(acc + zn, -f);
-                }
-            }
-        }
-        atomicAdd(&aw[zw], own);
-    }
-    __syncthreads();
-    // flush the window: 4 consecutive cells per thread and step
-    const bool vec_ok = (nx % 4) == 0 && ((uintptr_t)acc % 16) == 0;
-    for (int c4 = threadIdx.x; c4 < WH * WW / 4; c4 += NT) {
-        const int wy = c4 / (WW / 4), wx = (c4 % (WW / 4)) * 4;
-        const float4 v = *reinterpret_cast<const float4 *>(&aw[wy * P + wx]);
-        if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
-        int gy = y0 - HALO + wy;
-        const int gx = x0 - HALO + wx;
-        if (periodic) gy = wrap(gy, ny);
-        else if (gy < 0 || gy >= ny) continue;
-        if (vec_ok && gx >= 0 && gx + 3 < nx) {
-            red_add_v4(acc + (int64_t)gy * nx + gx, v.x, v.y, v.z, v.w);
-        } else {
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (vv[t] == 0.f) continue;
-                int xx = gx + t;
-                if (periodic) xx = wrap(xx, nx);
-                else if (xx < 0 || xx >= nx) continue;
-                red_add(acc + (int64_t)gy * nx + xx, vv[t]);
-            }
-        }
-    }
+    op::tile2d<UT, TW, TH, NT, WX, F16W>(nx, ny, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TW,
+                                         blockIdx.y * TH, smem);
 }
 
 // ---- direct scatter (FP64 in 2D) ----------------------------------------
@@ -258,37 +79,8 @@ __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, i
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
                                                        const UT *__restrict__ u, AT *__restrict__ Au) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, zc = blockIdx.z;
     if (x >= nx) return;
-    const int64_t z = ((int64_t)zc * ny + y) * nx + x;
-    const char4 b[3] = {offs[3 * z], offs[3 * z + 1], offs[3 * z + 2]};
-    int c[6][3];
-    selling_offsets(b, c);
-    AT w[6];
-    load_weights<AT, 6>(wbase, wt, z, w);
-    const AT uz = to_acc(u[z]);
-    AT acc = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const AT wq = scale * w[q];
-        if (wq == (AT)0) continue;
-#pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            int xn = x + s * c[q][0], yn = y + s * c[q][1], zn = zc + s * c[q][2];
-            if (bc == ADLBR_PERIODIC) {
-                xn = wrap(xn, nx);
-                yn = wrap(yn, ny);
-                zn = wrap(zn, nz);
-            } else if (xn < 0 || xn >= nx || yn < 0 || yn >= ny || zn < 0 || zn >= nz) {
-                continue;
-            }
-            const int64_t zz = ((int64_t)zn * ny + yn) * nx + xn;
-            const AT flux = wq * (uz - to_acc(u[zz]));
-            acc += flux;
-            red_add(Au + zz, -flux);
-        }
-    }
-    red_add(Au + z, acc);
+    op::point3d<UT, AT>(nx, ny, nz, bc, scale, offs, wbase, wt, u, Au, x, blockIdx.y, blockIdx.z);
 }
 
 // u <- u - acc   (acc holds dt A u).  The accumulator is cleared by a

@@ -1,0 +1,392 @@
+// Batched explicit steps over images and volumes of uneven sizes (not in the
+// paper: the serving form of its explicit scheme, Sec. 4.4, u <- u - dt A u
+// per item).
+//
+// A batch fixes its items (stencil handles, FP32 u buffers, time steps) and
+// owns one accumulator array for all of them.  One step is
+//   memset (all accumulators and the tile counter)
+//   -> one persistent kernel over a work list of tiles of every item: 2D
+//      tiles through the shared-window operator (op::tile2d), 3D blocks
+//      through the per-point scatter (op::point3d); tiles are handed out by
+//      an atomic counter, so uneven items balance across the SMs
+//   -> one finalize kernel over chunks of every item (u -= acc).
+// The step is recorded once as a CUDA graph and replayed.  The tile shapes
+// (2D tile, 3D block) come from an autotuner that times the accumulate
+// kernel of every candidate on the batch itself (the accumulate kernel
+// writes only the batch's accumulator, so tuning leaves u untouched).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "operator.cuh"
+
+struct adlbr_batch_item {
+    int dim, bc, nx, ny, nz;
+    adlbr_dtype wt;
+    const void *offs;
+    const void *w;
+    float *u;
+    float *acc;
+    float scale;
+    int64_t N;
+};
+
+struct adlbr_batch_tile {
+    int item, x0, y0, z0;
+};
+
+struct adlbr_batch_chunk {
+    int item;
+    int64_t start, len;
+};
+
+struct adlbr_batch {
+    int device;
+    int n_items;
+    int cand;                    // chosen shape candidate
+    double tuned_ms;             // its accumulate time
+    int64_t points;
+    adlbr_batch_item *items;     // device
+    adlbr_batch_tile *tiles;     // device (for the chosen shape)
+    int n_tiles;
+    adlbr_batch_chunk *chunks;   // device
+    int n_chunks;
+    float *acc;                  // device, sum of N_i floats + tile counter
+    size_t acc_bytes;
+    unsigned *counter;           // inside acc's allocation
+    int grid;                    // persistent CTAs of the accumulate kernel
+    int sms;
+    adlbr::ChunkGraph *graph;
+    std::vector<adlbr_batch_item> host_items;
+};
+
+namespace adlbr {
+
+namespace {
+
+constexpr int BNT = 256;             // threads per CTA of the batched kernels
+constexpr int kChunk = 1 << 16;      // finalize chunk (floats)
+
+struct Shape {
+    int tw, th;        // 2D tile
+    int bx, by, bz;    // 3D block (bz planes per thread)
+};
+// candidates of the autotuner (each one an instantiation of the kernel)
+constexpr Shape kShapes[] = {{64, 32, 32, 8, 4}, {64, 16, 32, 8, 4}, {32, 32, 32, 8, 4},
+                             {128, 16, 32, 8, 4}, {64, 32, 64, 4, 4}, {64, 32, 32, 8, 8}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int TW, int TH, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BNT) batch_accumulate_kernel(const adlbr_batch_item *__restrict__ items,
+                                                               const adlbr_batch_tile *__restrict__ tiles,
+                                                               int n_tiles, unsigned *counter) {
+    static_assert(BX * BY == BNT, "one thread per (x, y) of a 3D block");
+    constexpr int WX = 16;
+    using T = op::Tile<TW, TH, BNT, WX>;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();   // every thread has read `next` of the previous round
+        if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = next;
+        if (t >= n_tiles) return;
+        const adlbr_batch_tile tl = tiles[t];
+        const adlbr_batch_item it = items[tl.item];
+        if (it.dim == 2) {
+            if (it.wt == ADLBR_F16)
+                op::tile2d<float, TW, TH, BNT, WX, true>(it.nx, it.ny, it.bc, it.scale,
+                                                         (const short4 *)it.offs, it.w, it.wt, it.u,
+                                                         it.acc, tl.x0, tl.y0, smem);
+            else
+                op::tile2d<float, TW, TH, BNT, WX, false>(it.nx, it.ny, it.bc, it.scale,
+                                                          (const short4 *)it.offs, it.w, it.wt, it.u,
+                                                          it.acc, tl.x0, tl.y0, smem);
+        } else {
+            const int x = tl.x0 + (int)threadIdx.x % BX, y = tl.y0 + (int)threadIdx.x / BX;
+            if (x < it.nx && y < it.ny)
+                for (int k = 0; k < BZ; ++k) {
+                    const int zc = tl.z0 + k;
+                    if (zc >= it.nz) break;
+                    op::point3d<float, float>(it.nx, it.ny, it.nz, it.bc, it.scale,
+                                              (const char4 *)it.offs, it.w, it.wt, it.u, it.acc, x, y, zc);
+                }
+        }
+    }
+    (void)sizeof(T);
+}
+
+__global__ void __launch_bounds__(BNT) batch_finalize_kernel(const adlbr_batch_item *__restrict__ items,
+                                                             const adlbr_batch_chunk *__restrict__ chunks,
+                                                             int n_chunks) {
+    for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const adlbr_batch_chunk ch = chunks[c];
+        const adlbr_batch_item it = items[ch.item];
+        float *u = it.u + ch.start;
+        const float *a = it.acc + ch.start;
+        if ((((uintptr_t)u | (uintptr_t)a) & 15) == 0 && (ch.len & 3) == 0) {
+            float4 *u4 = reinterpret_cast<float4 *>(u);
+            const float4 *a4 = reinterpret_cast<const float4 *>(a);
+            for (int64_t i = threadIdx.x; i < ch.len / 4; i += BNT) {
+                const float4 av = a4[i], uv = u4[i];
+                u4[i] = make_float4(uv.x - av.x, uv.y - av.y, uv.z - av.z, uv.w - av.w);
+            }
+        } else {
+            for (int64_t i = threadIdx.x; i < ch.len; i += BNT) u[i] -= a[i];
+        }
+    }
+}
+
+template <int TW, int TH, int BX, int BY, int BZ>
+size_t accumulate_smem() {
+    using T = op::Tile<TW, TH, BNT, 16>;
+    return 2 * (size_t)T::P * T::WH * sizeof(float);
+}
+
+// Work list of tiles for shape sh: 2D items by TW x TH tiles, 3D items by
+// BX x BY x BZ blocks; the largest items first.
+std::vector<adlbr_batch_tile> make_tiles(const std::vector<adlbr_batch_item> &items, const Shape &sh) {
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < items.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a].N > items[b].N; });
+    std::vector<adlbr_batch_tile> out;
+    for (int i : order) {
+        const adlbr_batch_item &it = items[i];
+        if (it.dim == 2) {
+            for (int y = 0; y < it.ny; y += sh.th)
+                for (int x = 0; x < it.nx; x += sh.tw) out.push_back({i, x, y, 0});
+        } else {
+            for (int z = 0; z < it.nz; z += sh.bz)
+                for (int y = 0; y < it.ny; y += sh.by)
+                    for (int x = 0; x < it.nx; x += sh.bx) out.push_back({i, x, y, z});
+        }
+    }
+    return out;
+}
+
+// prepare = true: set the kernel's shared-memory limit and compute the
+// persistent grid (outside any graph capture); false: launch it.
+template <int TW, int TH, int BX, int BY, int BZ>
+adlbr_status acc_t(adlbr_batch *b, bool prepare, cudaStream_t st) {
+    auto kern = batch_accumulate_kernel<TW, TH, BX, BY, BZ>;
+    const size_t smem = accumulate_smem<TW, TH, BX, BY, BZ>();
+    if (prepare) {
+        ADLBR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        ADLBR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BNT, smem));
+        b->grid = std::max(1, std::min(b->n_tiles, std::max(1, per_sm) * b->sms));
+        return ADLBR_OK;
+    }
+    kern<<<b->grid, BNT, smem, st>>>(b->items, b->tiles, b->n_tiles, b->counter);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status acc(adlbr_batch *b, int cand, bool prepare, cudaStream_t st) {
+    switch (cand) {
+    case 0: return acc_t<64, 32, 32, 8, 4>(b, prepare, st);
+    case 1: return acc_t<64, 16, 32, 8, 4>(b, prepare, st);
+    case 2: return acc_t<32, 32, 32, 8, 4>(b, prepare, st);
+    case 3: return acc_t<128, 16, 32, 8, 4>(b, prepare, st);
+    case 4: return acc_t<64, 32, 64, 4, 4>(b, prepare, st);
+    case 5: return acc_t<64, 32, 32, 8, 8>(b, prepare, st);
+    }
+    return fail(ADLBR_E_ARG, "bad shape candidate %d", cand);
+}
+
+// Work list of candidate `cand` on the device and its launch geometry.
+adlbr_status use_shape(adlbr_batch *b, int cand, cudaStream_t st);
+
+adlbr_status upload_tiles(adlbr_batch *b, const std::vector<adlbr_batch_tile> &t, cudaStream_t st) {
+    if (b->tiles) cudaFree(b->tiles);
+    b->tiles = nullptr;
+    ADLBR_CUDA(cudaMalloc(&b->tiles, std::max<size_t>(1, t.size()) * sizeof(adlbr_batch_tile)));
+    ADLBR_CUDA(cudaMemcpyAsync(b->tiles, t.data(), t.size() * sizeof(adlbr_batch_tile),
+                               cudaMemcpyHostToDevice, st));
+    ADLBR_CUDA(cudaStreamSynchronize(st));
+    b->n_tiles = (int)t.size();
+    return ADLBR_OK;
+}
+
+adlbr_status use_shape(adlbr_batch *b, int cand, cudaStream_t st) {
+    if (adlbr_status e = upload_tiles(b, make_tiles(b->host_items, kShapes[cand]), st)) return e;
+    return acc(b, cand, true, st);
+}
+
+// One step, enqueued on st (also what the graph records).
+adlbr_status enqueue_step(adlbr_batch *b, cudaStream_t st) {
+    ADLBR_CUDA(cudaMemsetAsync(b->acc, 0, b->acc_bytes, st));
+    if (adlbr_status e = acc(b, b->cand, false, st)) return e;
+    batch_finalize_kernel<<<std::max(1, std::min(b->n_chunks, 4 * b->sms)), BNT, 0, st>>>(
+        b->items, b->chunks, b->n_chunks);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+void free_batch(adlbr_batch *b) {
+    if (!b) return;
+    delete b->graph;
+    if (b->items) cudaFree(b->items);
+    if (b->tiles) cudaFree(b->tiles);
+    if (b->chunks) cudaFree(b->chunks);
+    if (b->acc) cudaFree(b->acc);
+    delete b;
+}
+
+}  // namespace
+
+}  // namespace adlbr
+
+using namespace adlbr;
+
+extern "C" {
+
+adlbr_status adlbr_batch_create(int n_items, adlbr_stencils *const *s, float *const *u, const double *dt,
+                                int autotune, adlbr_batch **out, cudaStream_t stream) {
+    if (!out) return fail(ADLBR_E_ARG, "null output");
+    *out = nullptr;
+    if (n_items < 1 || !s || !u || !dt) return fail(ADLBR_E_ARG, "empty batch or null arrays");
+    int dev = 0;
+    ADLBR_CUDA(cudaGetDevice(&dev));
+    adlbr_batch *b = new adlbr_batch();
+    b->device = dev;
+    b->n_items = n_items;
+    if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) b->sms = 1;
+    b->cand = 0;
+    b->tuned_ms = 0.0;
+    // items and accumulator layout (each item's accumulator 16-byte aligned)
+    int64_t off = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const adlbr_stencils *h = s[i];
+        if (!h || !u[i] || !(dt[i] >= 0.0)) {
+            free_batch(b);
+            return fail(ADLBR_E_ARG, "item %d: null handle / buffer or bad dt", i);
+        }
+        if (h->device != dev) {
+            free_batch(b);
+            return fail(ADLBR_E_ARG, "item %d lives on device %d, current device is %d", i, h->device, dev);
+        }
+        adlbr_batch_item it = {};
+        it.dim = h->dim;
+        it.bc = h->bc;
+        it.nx = (int)h->n[0];
+        it.ny = (int)h->n[1];
+        it.nz = h->dim == 3 ? (int)h->n[2] : 1;
+        it.wt = h->w_t;
+        it.offs = h->offs;
+        it.w = h->w;
+        it.u = u[i];
+        it.scale = (float)dt[i];
+        it.N = h->N;
+        it.acc = reinterpret_cast<float *>((uintptr_t)off);   // offset for now
+        off += (h->N + 3) / 4 * 4;
+        b->points += h->N;
+        b->host_items.push_back(it);
+    }
+    b->acc_bytes = (size_t)off * sizeof(float) + 256;
+    cudaError_t ce = cudaMalloc(&b->acc, b->acc_bytes);
+    if (ce != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(ce, "cudaMalloc (batch accumulator)");
+    }
+    b->counter = reinterpret_cast<unsigned *>(b->acc + off);
+    for (auto &it : b->host_items) it.acc = b->acc + (int64_t)(uintptr_t)it.acc;
+    // finalize chunks
+    std::vector<adlbr_batch_chunk> chunks;
+    for (int i = 0; i < n_items; ++i)
+        for (int64_t st = 0; st < b->host_items[i].N; st += kChunk)
+            chunks.push_back({i, st, std::min<int64_t>(kChunk, b->host_items[i].N - st)});
+    b->n_chunks = (int)chunks.size();
+    adlbr_status e = ADLBR_OK;
+#define BCHECK(x)                                   \
+    do {                                            \
+        cudaError_t c_ = (x);                       \
+        if (c_ != cudaSuccess) {                    \
+            free_batch(b);                          \
+            return cuda_fail(c_, #x);                \
+        }                                           \
+    } while (0)
+    BCHECK(cudaMalloc(&b->items, n_items * sizeof(adlbr_batch_item)));
+    BCHECK(cudaMalloc(&b->chunks, chunks.size() * sizeof(adlbr_batch_chunk)));
+    BCHECK(cudaMemcpyAsync(b->items, b->host_items.data(), n_items * sizeof(adlbr_batch_item),
+                           cudaMemcpyHostToDevice, stream));
+    BCHECK(cudaMemcpyAsync(b->chunks, chunks.data(), chunks.size() * sizeof(adlbr_batch_chunk),
+                           cudaMemcpyHostToDevice, stream));
+    BCHECK(cudaStreamSynchronize(stream));
+    // autotune: time the accumulate kernel of every candidate shape
+    int best = 0;
+    if (autotune) {
+        cudaEvent_t e0, e1;
+        BCHECK(cudaEventCreate(&e0));
+        BCHECK(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (int c = 0; c < kNumShapes && e == ADLBR_OK; ++c) {
+            if ((e = use_shape(b, c, stream))) break;
+            float ms_min = 1e30f;
+            for (int r = 0; r < 4 && e == ADLBR_OK; ++r) {   // first round warms up
+                cudaMemsetAsync(b->acc, 0, b->acc_bytes, stream);
+                cudaEventRecord(e0, stream);
+                e = acc(b, c, false, stream);
+                cudaEventRecord(e1, stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best_ms) best_ms = ms_min, best = c;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->tuned_ms = best_ms;
+        if (e != ADLBR_OK) {
+            free_batch(b);
+            return e;
+        }
+    }
+    b->cand = best;
+    if ((e = use_shape(b, best, stream))) {
+        free_batch(b);
+        return e;
+    }
+    // record one step as a graph
+    b->graph = new ChunkGraph();
+    e = b->graph->capture([&](cudaStream_t cs) { return enqueue_step(b, cs); });
+    if (e != ADLBR_OK) {
+        free_batch(b);
+        return e;
+    }
+#undef BCHECK
+    *out = b;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_batch_step(adlbr_batch *b, int nsteps, cudaStream_t stream) {
+    if (!b) return fail(ADLBR_E_ARG, "null batch");
+    if (nsteps < 0) return fail(ADLBR_E_ARG, "bad nsteps");
+    int dev = -1;
+    ADLBR_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(ADLBR_E_ARG, "current device %d is not the batch's device %d", dev, b->device);
+    for (int k = 0; k < nsteps; ++k) ADLBR_CUDA(cudaGraphLaunch(b->graph->exec, stream));
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_batch_config(const adlbr_batch *b, int *shape_out, double *tuned_ms, int64_t *points,
+                                int *n_tiles) {
+    if (!b) return fail(ADLBR_E_ARG, "null batch");
+    if (shape_out) {
+        const Shape &sh = kShapes[b->cand];
+        shape_out[0] = sh.tw, shape_out[1] = sh.th;
+        shape_out[2] = sh.bx, shape_out[3] = sh.by, shape_out[4] = sh.bz;
+    }
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    if (points) *points = b->points;
+    if (n_tiles) *n_tiles = b->n_tiles;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_batch_destroy(adlbr_batch *b) {
+    free_batch(b);
+    return ADLBR_OK;
+}
+
+}  // extern "C"

@@ -123,6 +123,36 @@ def smooth_field2d(ny, nx, seed, kappa_min=1.0, kappa_max=50.0, lattice=16):
     return D_from_angle(theta, kappa)
 
 
+def smooth_field2d_torch(ny, nx, seed, kappa_min=1.0, kappa_max=50.0, lattice=16, device="cuda",
+                        dtype=None):
+    """smooth_field2d evaluated with torch on `device` (FP64 arithmetic, the
+    same lattice draws); for large benchmark inputs.  Returns a tensor
+    (3, ny, nx) of `dtype` (default float32)."""
+    import torch
+    g = rng(seed)
+    th = g.uniform(0, np.pi, (lattice, lattice))
+    lk = g.uniform(np.log(kappa_min), np.log(kappa_max), (lattice, lattice))
+    iy, fy = _lattice_coords(ny, lattice)
+    ix, fx = _lattice_coords(nx, lattice)
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device)
+    iy, ix, fy, fx = (torch.as_tensor(iy, device=device), torch.as_tensor(ix, device=device),
+                      T(fy)[:, None], T(fx)[None, :])
+
+    def interp(a):
+        a = T(a)
+        a00 = a[iy][:, ix]
+        a01 = a[iy][:, ix + 1]
+        a10 = a[iy + 1][:, ix]
+        a11 = a[iy + 1][:, ix + 1]
+        return (1 - fy) * ((1 - fx) * a00 + fx * a01) + fy * ((1 - fx) * a10 + fx * a11)
+
+    theta = 0.5 * torch.atan2(interp(np.sin(2 * th)), interp(np.cos(2 * th)))
+    lam2 = 1.0 / torch.exp(interp(lk)) ** 2
+    c, s_ = torch.cos(theta), torch.sin(theta)
+    D = torch.stack([c * c + lam2 * s_ * s_, (1.0 - lam2) * c * s_, s_ * s_ + lam2 * c * c])
+    return D.to(dtype or torch.float32)
+
+
 def batch_items(seed=100, n_images=64, n_volumes=8, img_sides=(256, 2048), vol_sides=(64, 192),
                 kappa=(5.0, 100.0)):
     """Uneven batch: per item a dict with its shape, tensor-field seed and

@@ -1,0 +1,99 @@
+"""Batched explicit steps over uneven 2D and 3D items: parity with the
+single-grid step and with the FP64 oracle, autotuned and fixed shapes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1301_3925_gb300 import adlbr as ab
+
+from gpu_helpers import build, dev, export, torch
+
+pytestmark = pytest.mark.gpu
+
+# (shape, boundary, weight type, field seed)
+ITEMS = [((50, 70), ab.NEUMANN, ab.F16, 1), ((33, 129), ab.PERIODIC, ab.F32, 2),
+         ((96, 64), ab.NEUMANN, ab.F64, 3), ((13, 17, 19), ab.NEUMANN, ab.F16, 4),
+         ((8, 10, 12), ab.PERIODIC, ab.F32, 5), ((130, 257), ab.NEUMANN, ab.F16, 6)]
+
+
+def _field(shape, seed):
+    if len(shape) == 2:
+        return synth.smooth_field2d(*shape, seed=seed, kappa_min=1, kappa_max=40, lattice=6)
+    n = max(shape)
+    return synth.needle_field3d(n, seed=seed, kappa=12.0)[:, :shape[0], :shape[1], :shape[2]]
+
+
+def _setup():
+    t = torch()
+    hs, us, dts, seen = [], [], [], []
+    for k, (shape, bc, wt, seed) in enumerate(ITEMS):
+        h, D, _ = build(_field(shape, seed), shape, t.float32, wt, bc)
+        hs.append(h)
+        seen.append(D)
+        dts.append(0.9 / ab.adlbr_stencils_max_diag(h))
+        us.append(dev(synth.u_uniform(shape, 10 + k).ravel(), t.float32))
+    return hs, us, dts, seen
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_matches_single_grid_steps(autotune):
+    t = torch()
+    hs, us, dts, _ = _setup()
+    ref = [u.clone() for u in us]
+    b = None
+    try:
+        for h, u, d in zip(hs, ref, dts):
+            scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.F32), dtype=t.uint8, device="cuda")
+            ab.adlbr_step_explicit(h, u, scratch, ab.F32, d, 5)
+        b = ab.adlbr_batch_create(hs, us, dts, autotune=autotune)
+        shape, ms, pts, ntiles = ab.adlbr_batch_config(b)
+        assert pts == sum(int(np.prod(s)) for s, _, _, _ in ITEMS) and ntiles > 0
+        assert (ms > 0) == autotune
+        if not autotune:
+            assert shape == (64, 32, 32, 8, 4)
+        ab.adlbr_batch_step(b, 5)
+        t.cuda.synchronize()
+        for k, (u, r) in enumerate(zip(us, ref)):
+            err = (u - r).abs().max().item() / r.abs().max().item()
+            assert err <= 1e-6, (k, ITEMS[k], err)
+    finally:
+        if b:
+            ab.adlbr_batch_destroy(b)
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
+
+
+def test_batch_matches_oracle():
+    t = torch()
+    hs, us, dts, seen = _setup()
+    u0 = [u.double().cpu().numpy() for u in us]
+    b = None
+    try:
+        stencils = [export(h, shape, wt) for h, (shape, _, wt, _) in zip(hs, ITEMS)]
+        b = ab.adlbr_batch_create(hs, us, dts)
+        ab.adlbr_batch_step(b, 3)
+        t.cuda.synchronize()
+        out = [u.double().cpu().numpy() for u in us]
+    finally:
+        if b:
+            ab.adlbr_batch_destroy(b)
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
+    for k, ((shape, bc, wt, _), (oo, ow)) in enumerate(zip(ITEMS, stencils)):
+        uo = oracle.step_explicit(shape, bc, oo, ow, u0[k].reshape(shape), dts[k], 3)
+        err = np.abs(out[k].reshape(shape) - uo).max() / np.abs(uo).max()
+        assert err <= 1e-5, (k, err)
+
+
+def test_batch_rejects_bad_input():
+    t = torch()
+    with pytest.raises(ab.AdlbrError):
+        ab.adlbr_batch_create([], [], [])
+    hs, us, dts, _ = _setup()
+    try:
+        with pytest.raises(ab.AdlbrError):
+            ab.adlbr_batch_create(hs[:1], us[:1], [-1.0])
+    finally:
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
