@@ -13,6 +13,7 @@
 // contribution to L2 directly.
 #include "operator.cuh"
 
+
 namespace adlbr {
 
 namespace {
@@ -71,6 +72,19 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, A
         }
     }
     red_add(Au + z, acc);
+}
+
+// 3D, FP32 accumulation: shared-memory window over a TX x TY x TZ block.
+template <typename UT, int TX, int TY, int TZ, bool F16W>
+__global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled(int nx, int ny, int nz, int bc, float scale,
+                                                         const char4 *__restrict__ offs,
+                                                         const void *__restrict__ wbase, adlbr_dtype wt,
+                                                         const UT *__restrict__ u, float *__restrict__ acc,
+                                                         const int *__restrict__ skip) {
+    extern __shared__ __align__(16) float smem[];
+    if (skip && *skip) return;
+    op::tile3d<UT, TX, TY, TZ, F16W>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
+                                     blockIdx.y * TY, blockIdx.z * TZ, smem);
 }
 
 template <typename UT, typename AT = typename UTraits<UT>::acc>
@@ -221,6 +235,19 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
                                                           (const short4 *)s->offs, s->w, s->w_t, u,
                                                           acc);
         }
+    } else if constexpr (sizeof(AT) == 4) {
+        constexpr int TX = 32, TY = 8, TZ = 4;   // 30 KB window, 5 CTAs per SM
+        constexpr size_t smem = 2 * op::Block3<TX, TY, TZ>::CELLS * sizeof(float);
+        static_assert(smem <= 48 * 1024, "default shared-memory limit");
+        dim3 grid(blocks_for(s->n[0], TX), blocks_for(s->n[1], TY), blocks_for(s->n[2], TZ));
+        if (s->w_t == ADLBR_F16)
+            apply3d_tiled<UT, TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
+                (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
+                s->w, s->w_t, u, acc, skip);
+        else
+            apply3d_tiled<UT, TX, TY, TZ, false><<<grid, TX * TY, smem, st>>>(
+                (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
+                s->w, s->w_t, u, acc, skip);
     } else {
         const int threads = 128;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);

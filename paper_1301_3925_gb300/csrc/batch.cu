@@ -6,8 +6,8 @@
 // owns one accumulator array for all of them.  One step is
 //   memset (all accumulators and the tile counter)
 //   -> one persistent kernel over a work list of tiles of every item: 2D
-//      tiles through the shared-window operator (op::tile2d), 3D blocks
-//      through the per-point scatter (op::point3d); tiles are handed out by
+//      tiles and 3D blocks through the shared-window operators (op::tile2d,
+//      op::tile3d); tiles are handed out by
 //      an atomic counter, so uneven items balance across the SMs
 //   -> one finalize kernel over chunks of every item (u -= acc).
 // The step is recorded once as a CUDA graph and replayed.  The tile shapes
@@ -102,15 +102,12 @@ __global__ void __launch_bounds__(BNT) batch_accumulate_kernel(const adlbr_batch
                 op::tile2d<float, TW, TH, BNT, WX, false>(it.nx, it.ny, it.bc, it.scale,
                                                           (const short4 *)it.offs, it.w, it.wt, it.u,
                                                           it.acc, tl.x0, tl.y0, smem);
+        } else if (it.wt == ADLBR_F16) {
+            op::tile3d<float, BX, BY, BZ, true>(it.nx, it.ny, it.nz, it.bc, it.scale, (const char4 *)it.offs,
+                                                it.w, it.wt, it.u, it.acc, tl.x0, tl.y0, tl.z0, smem);
         } else {
-            const int x = tl.x0 + (int)threadIdx.x % BX, y = tl.y0 + (int)threadIdx.x / BX;
-            if (x < it.nx && y < it.ny)
-                for (int k = 0; k < BZ; ++k) {
-                    const int zc = tl.z0 + k;
-                    if (zc >= it.nz) break;
-                    op::point3d<float, float>(it.nx, it.ny, it.nz, it.bc, it.scale,
-                                              (const char4 *)it.offs, it.w, it.wt, it.u, it.acc, x, y, zc);
-                }
+            op::tile3d<float, BX, BY, BZ, false>(it.nx, it.ny, it.nz, it.bc, it.scale, (const char4 *)it.offs,
+                                                 it.w, it.wt, it.u, it.acc, tl.x0, tl.y0, tl.z0, smem);
         }
     }
     (void)sizeof(T);
@@ -140,7 +137,9 @@ __global__ void __launch_bounds__(BNT) batch_finalize_kernel(const adlbr_batch_i
 template <int TW, int TH, int BX, int BY, int BZ>
 size_t accumulate_smem() {
     using T = op::Tile<TW, TH, BNT, 16>;
-    return 2 * (size_t)T::P * T::WH * sizeof(float);
+    const size_t s2 = 2 * (size_t)T::P * T::WH * sizeof(float);
+    const size_t s3 = 2 * (size_t)op::Block3<BX, BY, BZ>::CELLS * sizeof(float);
+    return s2 > s3 ? s2 : s3;
 }
 
 // Work list of tiles for shape sh: 2D items by TW x TH tiles, 3D items by

@@ -209,6 +209,181 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
 }
 
 
+// ---- 3D, shared-memory window --------------------------------------------
+// A CTA of TX * TY threads owns a TX x TY x TZ block (one thread per (x, y),
+// looping over z).  u is staged over the block plus a halo of H3 points (XL
+// along x, so that window rows start on a 16-byte boundary) and pushes stay
+// in a shared accumulator over the same window; 98% of the edges of the
+// kappa = 20 needle stencils are at most 2 points long (Chebyshev).
+constexpr int H3 = 2, XL = 4;
+
+template <int TX, int TY, int TZ>
+struct Block3 {
+    static_assert(TX % 4 == 0, "whole float4 rows");
+    static constexpr int WX = TX + 2 * XL, WY = TY + 2 * H3, WZ = TZ + 2 * H3;
+    static constexpr int PX = WX;                     // row pitch
+    static constexpr int PY = WY * PX;                // plane pitch
+    static constexpr int CELLS = WZ * PY;
+};
+
+// Weights of 3D point z (8 lanes: six F16 weights and the meta lane) times
+// `scale`, widened as in weights_f16_scaled.
+__device__ __forceinline__ void weights6_f16_scaled(const void *wbase, int64_t z, float scale,
+                                                    float (&w)[6]) {
+    const uint4 r = reinterpret_cast<const uint4 *>(wbase)[z];
+    const int s = (int)(int8_t)(r.w >> 8);
+    const float c = __int_as_float((127 + s) << 23) * scale;
+    const unsigned h[6] = {r.x & 0xffffu, r.x >> 16, r.y & 0xffffu, r.y >> 16, r.z & 0xffffu, r.z >> 16};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = __uint_as_float(h[k] << 13) * 0x1p112f * c;
+}
+
+// acc += scale A u over the block at (x0, y0, z0); all TX * TY threads of
+// the CTA call it.  smem: 2 * Block3::CELLS floats, 16-byte aligned.
+template <typename UT, int TX, int TY, int TZ, bool F16W>
+__device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float scale,
+                                       const char4 *__restrict__ offs, const void *__restrict__ wbase,
+                                       adlbr_dtype wt, const UT *__restrict__ u, float *__restrict__ acc,
+                                       int x0, int y0, int z0, float *smem) {
+    using B = Block3<TX, TY, TZ>;
+    constexpr int WY = B::WY, WZ = B::WZ, PX = B::PX, PY = B::PY;
+    constexpr int NT = TX * TY;
+    float *uw = smem, *aw = smem + B::CELLS;
+    __syncthreads();   // the window of a previous block may still be read
+    const bool periodic = bc == ADLBR_PERIODIC;
+    const bool inside = periodic || (x0 >= H3 && y0 >= H3 && z0 >= H3 && x0 + TX + H3 <= nx &&
+                                     y0 + TY + H3 <= ny && z0 + TZ + H3 <= nz);
+    const int wx0 = x0 - XL;   // grid x of window column 0 (a multiple of 4)
+    const int64_t nxy = (int64_t)nx * ny;
+    // stage u (4 cells per step), zero the accumulator
+    const bool vec = std::is_same<UT, float>::value && (nx % 4) == 0 && !periodic &&
+                     ((uintptr_t)u % 16) == 0;
+    constexpr int Q = PX / 4;   // float4s per window row
+    for (int c4 = threadIdx.x; c4 < WZ * WY * Q; c4 += NT) {
+        const int wz = c4 / (WY * Q), rem = c4 - wz * (WY * Q);
+        const int wy = rem / Q, wx = (rem - wy * Q) * 4;
+        const int gz = z0 - H3 + wz, gy = y0 - H3 + wy, gx = wx0 + wx;
+        float v[4];
+        if (vec && (unsigned)gz < (unsigned)nz && (unsigned)gy < (unsigned)ny && gx >= 0 && gx + 3 < nx) {
+            const float4 q = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(u) +
+                                                               gz * nxy + (int64_t)gy * nx + gx);
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                int xx = gx + t, yy = gy, zz = gz;
+                v[t] = 0.f;
+                if (periodic) {
+                    xx = wrap(xx, nx);
+                    yy = wrap(yy, ny);
+                    zz = wrap(zz, nz);
+                } else if ((unsigned)xx >= (unsigned)nx || (unsigned)yy >= (unsigned)ny ||
+                           (unsigned)zz >= (unsigned)nz) {
+                    continue;
+                }
+                v[t] = to_acc(u[zz * nxy + (int64_t)yy * nx + xx]);
+            }
+        }
+        const int o = wz * PY + wy * PX + wx;
+        *reinterpret_cast<float4 *>(&uw[o]) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(&aw[o]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x < nx && y < ny) {
+#pragma unroll 2
+        for (int k = 0; k < TZ; ++k) {
+            const int zc = z0 + k;
+            if (zc >= nz) break;
+            const int64_t z = zc * nxy + (int64_t)y * nx + x;
+            const char4 b[3] = {offs[3 * z], offs[3 * z + 1], offs[3 * z + 2]};
+            int c[6][3];
+            selling_offsets(b, c);
+            float w[6];
+            if (F16W) {
+                weights6_f16_scaled(wbase, z, scale, w);
+            } else {
+                load_weights<float, 6>(wbase, wt, z, w);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) w[q] *= scale;
+            }
+            const int zw = (k + H3) * PY + (ty + H3) * PX + tx + XL;
+            const float uz = uw[zw];
+            float own = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float wq = w[q];
+                if (abs(c[q][0]) <= H3 && abs(c[q][1]) <= H3 && abs(c[q][2]) <= H3) {
+                    const int d = c[q][2] * PY + c[q][1] * PX + c[q][0];
+#pragma unroll
+                    for (int sg = -1; sg <= 1; sg += 2) {
+                        if (!inside) {
+                            const int xn = x + sg * c[q][0], yn = y + sg * c[q][1], zn = zc + sg * c[q][2];
+                            if ((unsigned)xn >= (unsigned)nx || (unsigned)yn >= (unsigned)ny ||
+                                (unsigned)zn >= (unsigned)nz)
+                                continue;
+                        }
+                        const int zn = zw + sg * d;
+                        const float f = wq * (uz - uw[zn]);
+                        own += f;
+                        atomicAdd(&aw[zn], -f);
+                    }
+                } else if (wq != 0.f) {
+#pragma unroll
+                    for (int sg = -1; sg <= 1; sg += 2) {
+                        int xn = x + sg * c[q][0], yn = y + sg * c[q][1], zn = zc + sg * c[q][2];
+                        if (periodic) {
+                            xn = wrap(xn, nx);
+                            yn = wrap(yn, ny);
+                            zn = wrap(zn, nz);
+                        } else if ((unsigned)xn >= (unsigned)nx || (unsigned)yn >= (unsigned)ny ||
+                                   (unsigned)zn >= (unsigned)nz) {
+                            continue;
+                        }
+                        const int64_t zz = zn * nxy + (int64_t)yn * nx + xn;
+                        const float f = wq * (uz - to_acc(u[zz]));
+                        own += f;
+                        red_add(acc + zz, -f);
+                    }
+                }
+            }
+            atomicAdd(&aw[zw], own);
+        }
+    }
+    __syncthreads();
+    // flush the window (4 cells per step)
+    const bool vec_ok = (nx % 4) == 0 && ((uintptr_t)acc % 16) == 0;
+    for (int c4 = threadIdx.x; c4 < WZ * WY * Q; c4 += NT) {
+        const int wz = c4 / (WY * Q), rem = c4 - wz * (WY * Q);
+        const int wy = rem / Q, wx = (rem - wy * Q) * 4;
+        const float4 v = *reinterpret_cast<const float4 *>(&aw[wz * PY + wy * PX + wx]);
+        if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+        int gz = z0 - H3 + wz, gy = y0 - H3 + wy;
+        const int gx = wx0 + wx;
+        if (periodic) {
+            gz = wrap(gz, nz);
+            gy = wrap(gy, ny);
+        } else if ((unsigned)gz >= (unsigned)nz || (unsigned)gy >= (unsigned)ny) {
+            continue;
+        }
+        float *row = acc + gz * nxy + (int64_t)gy * nx;
+        if (vec_ok && !periodic && gx >= 0 && gx + 3 < nx) {
+            red_add_v4(row + gx, v.x, v.y, v.z, v.w);
+        } else {
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (vv[t] == 0.f) continue;
+                int xx = gx + t;
+                if (periodic) xx = wrap(xx, nx);
+                else if (xx < 0 || xx >= nx) continue;
+                red_add(row + xx, vv[t]);
+            }
+        }
+    }
+}
+
 // Point (x, y, zc) of a 3D grid: its own edges into a register, the
 // opposite contributions and the own sum pushed to Au in L2.
 template <typename UT, typename AT>
