@@ -29,11 +29,6 @@ struct V2 {
     int x, y;
 };
 
-__device__ __forceinline__ float gram2(float sxx, float sxy, float syy, V2 u, V2 v) {
-    float ux = (float)u.x, uy = (float)u.y, vx = (float)v.x, vy = (float)v.y;
-    return sxx * ux * vx + sxy * (ux * vy + uy * vx) + syy * uy * vy;
-}
-
 // <u, adj(D) v> = c ux vx - b (ux vy + uy vx) + a uy vy, terms (x_k, n_k).
 template <typename T>
 __device__ __forceinline__ void terms2(T a, T b, T c, V2 u, V2 v, T (&x)[3], int (&n)[3]) {
@@ -81,13 +76,14 @@ __device__ __forceinline__ bool det_positive(double a, double b, double c) {
 __device__ __forceinline__ bool finite(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
-// S = adj(D) / max(a, c) in FP32, for the approximate reduction loop.
+// S = adj(D) / max(a, c) in FP32 (approximately: one reciprocal), for the
+// approximate reduction loop.
 __device__ __forceinline__ void scaled_adj(float a, float b, float c, float &sxx, float &sxy,
                                            float &syy) {
-    const float m = fmaxf(a, c);
-    sxx = c / m;
-    sxy = -b / m;
-    syy = a / m;
+    const float m = __frcp_rn(fmaxf(a, c));
+    sxx = c * m;
+    sxy = -b * m;
+    syy = a * m;
 }
 __device__ __forceinline__ void scaled_adj(double a, double b, double c, float &sxx, float &sxy,
                                            float &syy) {
@@ -95,6 +91,12 @@ __device__ __forceinline__ void scaled_adj(double a, double b, double c, float &
     sxx = (float)(c / m);
     sxy = (float)(-b / m);
     syy = (float)(a / m);
+}
+
+// <u, S v> for integer-valued float vectors (exact coordinates below 2^24).
+__device__ __forceinline__ float gramf(float sxx, float sxy, float syy, float ux, float uy, float vx,
+                                       float vy) {
+    return sxx * ux * vx + sxy * (ux * vy + uy * vx) + syy * uy * vy;
 }
 
 constexpr int kMaxReduce = 64;
@@ -124,24 +126,28 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
         return;
     }
 
-    // (i) approximate Lagrange reduction in FP32 on S / max(a, c)
+    // (i) approximate Lagrange reduction in FP32 on S / max(a, c): the basis
+    // vectors are kept as integer-valued floats, |f|_S^2 is carried over to
+    // the next |e|_S^2, and the quotient is approximate (the result is
+    // certified exactly below, so these shortcuts can only cost repair steps)
     float sxx, sxy, syy;
     scaled_adj(a, b, c, sxx, sxy, syy);
-    V2 e{1, 0}, f{0, 1};
+    float ex = 1.f, ey = 0.f, fx = 0.f, fy = 1.f;
+    float gff = syy;   // |f|_S^2 of f = (0, 1)
     for (int it = 0; it < kMaxReduce; ++it) {
-        float den = gram2(sxx, sxy, syy, f, f);
-        if (!(den > 0.f)) break;
-        float r = rintf(gram2(sxx, sxy, syy, e, f) / den);
-        r = fminf(fmaxf(r, -2048.f), 2048.f);
-        int q = (int)r;
-        V2 nf{e.x - q * f.x, e.y - q * f.y};
-        e = f;
-        f = nf;
-        if (abs(f.x) > kMaxCoord || abs(f.y) > kMaxCoord) break;
-        if (!(gram2(sxx, sxy, syy, e, e) > gram2(sxx, sxy, syy, f, f))) break;
+        if (!(gff > 0.f)) break;
+        const float gef = gramf(sxx, sxy, syy, ex, ey, fx, fy);
+        const float q = fminf(fmaxf(rintf(__fdividef(gef, gff)), -2048.f), 2048.f);
+        const float nx = fmaf(-q, fx, ex), ny = fmaf(-q, fy, ey);   // exact: integers below 2^24
+        const float gee = gff;
+        ex = fx, ey = fy, fx = nx, fy = ny;
+        if (fabsf(fx) > (float)kMaxCoord || fabsf(fy) > (float)kMaxCoord) break;
+        gff = gramf(sxx, sxy, syy, fx, fy, fx, fy);
+        if (!(gee > gff)) break;
     }
     // (ii) orientation of f
-    if (gram2(sxx, sxy, syy, e, f) > 0.f) f = V2{-f.x, -f.y};
+    if (gramf(sxx, sxy, syy, ex, ey, fx, fy) > 0.f) fx = -fx, fy = -fy;
+    V2 e{(int)ex, (int)ey}, f{(int)fx, (int)fy};
 
     // (iii) superbase, certified and repaired with exact signs
     V2 v[3] = {e, f, V2{-e.x - f.x, -e.y - f.y}};
