@@ -6,7 +6,7 @@ import oracle
 import synth
 from paper_1301_3925_gb300 import adlbr as ab
 
-from gpu_helpers import build, dev, torch
+from gpu_helpers import build, dev, export, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -162,3 +162,35 @@ def test_max_diag_matches_oracle(bc, dim):
     oo, ow = _oracle_stencils(seen, dim)
     ref = oracle.diag(shape, bc, oo, ow).max()
     assert abs(m - ref) <= 1e-5 * ref, (m, ref)
+
+
+def test_apply3d_full_size_sampled():
+    """256^3 needle stencils (F16 weights), FP32 u, the launch the benchmark
+    times: Au at sampled points against the oracle on a crop around each
+    point (the crop's half width exceeds the longest offset, so every pair
+    that touches the centre lies inside the crop)."""
+    t = torch()
+    n = 256
+    D = synth.needle_field3d(n, 2, kappa=20.0, dtype=np.float32)
+    h, seen, _ = build(D, (n, n, n), t.float32, ab.F16)
+    try:
+        go, gw = export(h, (n, n, n), ab.F16)
+        u = synth.u_uniform((n, n, n), 7)
+        Au, useen = _gpu_apply(h, u, t.float32)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    half = int(np.abs(go).max()) + 1     # crop half width beyond the longest offset
+    assert half <= 24
+    go = go.reshape(n, n, n, 6, 3)
+    gw = gw.reshape(n, n, n, 6)
+    scale = np.abs(Au).max()
+    rng = np.random.default_rng(2)
+    pts = [tuple(rng.integers(half, n - half, 3)) for _ in range(6)] + [(0, 0, 0), (n - 1, 5, n - 1)]
+    for z, y, x in pts:
+        z0, y0, x0 = (max(0, c - half) for c in (z, y, x))
+        z1, y1, x1 = (min(n, c + half + 1) for c in (z, y, x))
+        cs = (z1 - z0, y1 - y0, x1 - x0)
+        oo = go[z0:z1, y0:y1, x0:x1].reshape(-1, 6, 3)
+        ow = gw[z0:z1, y0:y1, x0:x1].reshape(-1, 6)
+        ref = oracle.apply(cs, oracle.NEUMANN, oo, ow, useen[z0:z1, y0:y1, x0:x1])
+        assert abs(Au[z, y, x] - ref[z - z0, y - y0, x - x0]) <= 1e-5 * scale

@@ -56,3 +56,30 @@ def test_cg_iteration_limit_reports_not_converged():
         assert ei.value.status == 5
     finally:
         ab.adlbr_stencils_destroy(h)
+
+
+def test_cg_full_size_2048():
+    """The benchmark's implicit step: 2048^2, kappa <= 50, dt = 200 / max A_zz,
+    tolerance 1e-6.  The true residual of the returned x is recomputed by the
+    oracle in FP64 with the library's own stencils (exported)."""
+    from gpu_helpers import export
+    t = torch()
+    n = 2048
+    D = synth.smooth_field2d_torch(n, n, 3, 1.0, 50.0, 16).reshape(3, -1).contiguous()
+    g = ab.grid((n, n))
+    h = ab.adlbr_build_stencils(g, D, ab.F32, ab.F32)
+    try:
+        dt = 200.0 / ab.adlbr_stencils_max_diag(h)
+        b = dev(synth.u_uniform((n, n), 3).ravel(), t.float32)
+        x = b.clone()
+        it, rel = ab.adlbr_step_implicit(h, b, x, dt, 1e-6, 4000)
+        oo, ow = export(h, (n, n), ab.F32)
+        xs = x.double().cpu().numpy().reshape(n, n)
+        bs = b.double().cpu().numpy().reshape(n, n)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    res = bs - (xs + dt * oracle.apply((n, n), oracle.NEUMANN, oo, ow, xs))
+    true_rel = np.linalg.norm(res) / np.linalg.norm(bs)
+    assert true_rel <= 1e-5, true_rel
+    assert abs(rel - true_rel) <= 0.05 * true_rel + 1e-9
+    assert 50 <= it <= 400, it

@@ -107,3 +107,22 @@ def test_build2d_full_size_sampled():
     assert np.all(st == 0)
     assert np.array_equal(go[idx], oo)
     assert np.all(np.abs(gw[idx] - ow) <= weight_tol(ow, ab.F16, None))
+
+
+def test_build3d_full_size_sampled():
+    """256^3 needle field (the 3D workload, FP32 D, F16 weights) built in one
+    launch; a random sample of points against the oracle point by point."""
+    t = torch()
+    n = 256
+    D = synth.needle_field3d(n, 2, kappa=20.0, dtype=np.float32)
+    h, seen, _ = build(D, (n, n, n), t.float32, ab.F16)
+    try:
+        ab.adlbr_stencils_check(h)
+        go, gw = export(h, (n, n, n), ab.F16)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    idx = np.random.default_rng(1).choice(n ** 3, 50_000, replace=False)
+    oo, ow, st, _ = oracle.build3d(seen.reshape(6, -1)[:, idx])
+    assert np.all(st == 0)
+    assert np.array_equal(go[idx], oo)
+    assert np.all(np.abs(gw[idx] - ow) <= weight_tol(ow, ab.F16, None))
