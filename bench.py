@@ -553,30 +553,56 @@ def main():
                  "frac_hbm": apply_gbs / peak, "bytes_per_point": 24,
                  "stencils": "CED kappa <= 100 (4096^2 fingerprint)"}
 
-    # end to end through the C ABI with host buffers
+    # End to end through the C ABI with host buffers: every step copies its
+    # input image from pinned host memory and reads its result back.  As a
+    # serving loop would, the copies of one request overlap the compute of
+    # its neighbours: a host-to-device stream, the compute stream and a
+    # device-to-host stream, three device buffers in rotation.
     e2e = None
     if not args.no_e2e:
+        Ke = max(6, min(K, 50))
         host = torch.from_numpy(img.ravel()).pin_memory()
-        out = torch.empty_like(host).pin_memory()
-        for _ in range(2):
-            u.copy_(host, non_blocking=True)
-            step()
-            out.copy_(u, non_blocking=True)
+        outs = [torch.empty_like(host).pin_memory() for _ in range(3)]
+        bufs = [torch.empty_like(u) for _ in range(3)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def step_on(buf):
+            nonlocal h
+            ab.adlbr_ced_tensor(g, buf, Dbuf, *S, scratch)
+            h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
+            ab.adlbr_step_explicit(h, buf, acc, ab.F32, CED["dt"], 1)
+
+        def run(n):
+            done_out = [None] * 3
+            for k in range(n):
+                j = k % 3
+                with torch.cuda.stream(s_in):
+                    if done_out[j] is not None:
+                        s_in.wait_event(done_out[j])   # the buffer's previous result is read out
+                    bufs[j].copy_(host, non_blocking=True)
+                    ev_in = torch.cuda.Event()
+                    ev_in.record(s_in)
+                stream.wait_event(ev_in)
+                step_on(bufs[j])
+                ev_c = torch.cuda.Event()
+                ev_c.record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_c)
+                    outs[j].copy_(bufs[j], non_blocking=True)
+                    done_out[j] = torch.cuda.Event()
+                    done_out[j].record(s_out)
+
+        run(3)
         torch.cuda.synchronize()
-        Ke = max(5, min(K, 50))
         barrier(ws)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(Ke):
-            u.copy_(host, non_blocking=True)
-            step()
-            out.copy_(u, non_blocking=True)
-        b.record(stream)
+        t_e0 = time.perf_counter()
+        run(Ke)
         torch.cuda.synchronize()
-        e2e_ms = allmax(ws, a.elapsed_time(b)) / Ke
+        e2e_ms = allmax(ws, (time.perf_counter() - t_e0) * 1e3) / Ke
+        assert torch.equal(outs[(Ke - 1) % 3], bufs[(Ke - 1) % 3].cpu())
         e2e = {"value": job_value(ws, N, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N}
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N,
+               "pipeline": "H2D / compute / D2H on three streams, three device buffers"}
 
     implicit = None if args.no_implicit or rank != 0 else implicit_measurement(peak)
     volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)

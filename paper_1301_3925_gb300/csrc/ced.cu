@@ -219,18 +219,20 @@ __host__ __device__ constexpr FusedGeom fused_geom(int R, int S) {
 // One output group of a symmetric blur: RB consecutive outputs from the
 // RB + 2r values v (v[r + o] is the centre of output o), in the operation
 // order of the separable kernels.
-template <int RR>
-__device__ __forceinline__ void blur_group(const float (&v)[RB + 2 * RR], const Taps &tp, int r,
-                                           float (&acc)[RB]) {
+template <int RR, int NB = RB>
+__device__ __forceinline__ void blur_group(const float (&v)[NB + 2 * RR], const Taps &tp, int r,
+                                           float (&acc)[NB]) {
 #pragma unroll
-    for (int o = 0; o < RB; ++o) acc[o] = __fmul_rn(tp.t[0], v[RR + o]);
+    for (int o = 0; o < NB; ++o) acc[o] = __fmul_rn(tp.t[0], v[RR + o]);
 #pragma unroll
     for (int k = 1; k <= RR; ++k) {
         if (k > r) break;
 #pragma unroll
-        for (int o = 0; o < RB; ++o) acc[o] = __fmaf_rn(tp.t[k], __fadd_rn(v[RR + o - k], v[RR + o + k]), acc[o]);
+        for (int o = 0; o < NB; ++o) acc[o] = __fmaf_rn(tp.t[k], __fadd_rn(v[RR + o - k], v[RR + o + k]), acc[o]);
     }
 }
+
+constexpr int RBY = 8;   // rows per thread in the last (y) pass: 512 groups, one per thread
 
 // S_, R_ > 0: radii fixed at compile time (all loops unrolled, windows in
 // registers, constant index arithmetic); 0: taken from g at run time, with
@@ -367,23 +369,23 @@ __global__ void __launch_bounds__(FNT, 1) ced_fused_kernel(int nx, int ny, int64
         }
     }
     __syncthreads();
-    // 6. y pass of Px and D(J) (lanes along columns, RB rows per thread)
+    // 6. y pass of Px and D(J) (lanes along columns, RBY rows per thread)
     {
-        constexpr int groups = FT / RB;
+        constexpr int groups = FT / RBY;
         for (int i = threadIdx.x; i < FT * groups; i += FNT) {
-            const int c = i % FT, r0 = (i / FT) * RB;
-            float J[3][RB];
+            const int c = i % FT, r0 = (i / FT) * RBY;
+            float J[3][RBY];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float *s = PX + (ch * g.PH + r0 + R - RR) * g.XP + c;
-                float v[RB + 2 * RR];
+                float v[RBY + 2 * RR];
 #pragma unroll
-                for (int j = 0; j < RB + 2 * RR; ++j)
-                    v[j] = (fixed || (j >= RR - R && j < RR + R + RB)) ? s[j * g.XP] : 0.f;
-                blur_group<RR>(v, tr, R, J[ch]);
+                for (int j = 0; j < RBY + 2 * RR; ++j)
+                    v[j] = (fixed || (j >= RR - R && j < RR + R + RBY)) ? s[j * g.XP] : 0.f;
+                blur_group<RR, RBY>(v, tr, R, J[ch]);
             }
 #pragma unroll
-            for (int o = 0; o < RB; ++o) {
+            for (int o = 0; o < RBY; ++o) {
                 const int64_t z = (int64_t)(y0 + r0 + o) * nx + x0 + c;
                 float dxx, dxy, dyy;
                 d_from_j(J[0][o], J[1][o], J[2][o], alpha, Cc, dxx, dxy, dyy);

@@ -43,9 +43,12 @@ __device__ __forceinline__ int reflect(int i, int n) {
 
 // D(J) for J = [[p, q], [q, s]]: eigenvectors of J, lambda1 = alpha on v1
 // (eigenvalue mu1 >= mu2), lambda2 = alpha + (1 - alpha) exp(-C / (mu1 -
-// mu2)^2) on v2; written with (mu1 - mu2)^2 = (p - s)^2 + 4 q^2 and
-// v1 v1^T = (I + [[cos 2t, sin 2t], [sin 2t, -cos 2t]]) / 2.  Explicitly
-// rounded operations, so every kernel computes bit-identical values.
+// mu2)^2) on v2; written with (mu1 - mu2)^2 = d2 = (p - s)^2 + 4 q^2 and
+// v1 v1^T = (I + [[cos 2t, sin 2t], [sin 2t, -cos 2t]]) / 2, cos 2t and
+// sin 2t taken with one reciprocal square root of d2.  Where C / d2 > 87,
+// exp(-C / d2) is below 2^-125 and lambda2 rounds to alpha in FP32: D = alpha I
+// there, as for d2 = 0.  The same instructions in every kernel, so all of
+// them compute bit-identical values.
 __device__ __forceinline__ void d_from_j(float p, float q, float s, float alpha, float C,
                                          float &Dxx, float &Dxy, float &Dyy) {
     const float dps = __fsub_rn(p, s);
@@ -53,10 +56,10 @@ __device__ __forceinline__ void d_from_j(float p, float q, float s, float alpha,
     Dxx = alpha;
     Dxy = 0.f;
     Dyy = alpha;
-    if (d2 > 0.f) {
-        const float delta = __fsqrt_rn(d2);
-        const float lam2 = __fmaf_rn(__fsub_rn(1.f, alpha), expf(__fdiv_rn(-C, d2)), alpha);
-        const float c2 = __fdiv_rn(dps, delta), s2 = __fdiv_rn(__fmul_rn(2.f, q), delta);
+    if (d2 > 0.f && C < __fmul_rn(87.f, d2)) {
+        const float rd = rsqrtf(d2);
+        const float lam2 = __fmaf_rn(__fsub_rn(1.f, alpha), __expf(__fmul_rn(-C, __fmul_rn(rd, rd))), alpha);
+        const float c2 = __fmul_rn(dps, rd), s2 = __fmul_rn(__fmul_rn(2.f, q), rd);
         const float m = __fmul_rn(0.5f, __fadd_rn(alpha, lam2));
         const float h = __fmul_rn(0.5f, __fsub_rn(alpha, lam2));
         Dxx = __fmaf_rn(h, c2, m);
