@@ -153,6 +153,21 @@ def smooth_field2d_torch(ny, nx, seed, kappa_min=1.0, kappa_max=50.0, lattice=16
     return D.to(dtype or torch.float32)
 
 
+def restoration_problem(N, kappa, alpha=1.0 / 3.0):
+    """The restoration test with a known solution (Sec. 5, "A test case with an
+    explicit solution") on the N x N cell-centred grid of [0,1)^2: the
+    tensor field D = [[1, s], [s, s^2 + kappa^-2]], s = 2 pi alpha sin(2 pi x),
+    and the transported stripe image v(x, y) = 1 if y + alpha cos(2 pi x) < 1/2.
+    Returns (D planes (3, N, N), v (N, N), the stripe coordinate
+    y + alpha cos(2 pi x) (N, N)); arrays indexed [y, x]."""
+    c = (np.arange(N) + 0.5) / N
+    X, Y = np.meshgrid(c, c)
+    s = 2 * np.pi * alpha * np.sin(2 * np.pi * X)
+    D = np.stack([np.ones_like(s), s, s * s + kappa ** -2.0])
+    Yf = Y + alpha * np.cos(2 * np.pi * X)
+    return D, (Yf < 0.5).astype(np.float64), Yf
+
+
 def batch_items(seed=100, n_images=64, n_volumes=8, img_sides=(256, 2048), vol_sides=(64, 192),
                 kappa=(5.0, 100.0)):
     """Uneven batch: per item a dict with its shape, tensor-field seed and

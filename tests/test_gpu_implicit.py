@@ -83,3 +83,34 @@ def test_cg_full_size_2048():
     assert true_rel <= 1e-5, true_rel
     assert abs(rel - true_rel) <= 0.05 * true_rel + 1e-9
     assert 50 <= it <= 400, it
+
+
+def test_restoration_against_exact_solution():
+    """The analytic restoration problem (Sec. 5) solved through the library:
+    F32 tensor, F32 weights, CG to 1e-6 at lambda N^2.  At N = 200 the errors
+    to the exact solution equal the oracle's (same scheme); they fall with N
+    (first order) up to N = 800."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_restoration import LAM, errors, exact
+    t = torch()
+    kappa = 10.0
+    errs = {}
+    for N in (200, 400, 800):
+        D, v, Yf = synth.restoration_problem(N, kappa)
+        h, seen, _ = build(D, (N, N), t.float32, ab.F32)
+        try:
+            vd = dev(v.ravel(), t.float32)
+            x = vd.clone()
+            ab.adlbr_step_implicit(h, vd, x, LAM * N * N, 1e-6, 5000)
+            xs = x.double().cpu().numpy().reshape(N, N)
+        finally:
+            ab.adlbr_stencils_destroy(h)
+        errs[N] = errors(xs, exact(Yf, kappa), N)
+        if N == 200:
+            oo, ow, st, _ = oracle.build2d(*seen.reshape(3, -1))
+            xo, _, _ = oracle.cg((N, N), oracle.NEUMANN, oo, ow, v, v, LAM * N * N, rtol=1e-9)
+            eo = errors(xo, exact(Yf, kappa), N)
+            assert np.allclose(errs[N], eo, rtol=1e-2), (errs[N], eo)
+    for a, b in ((200, 400), (400, 800)):
+        assert errs[a][0] / errs[b][0] >= 1.6 and errs[a][1] / errs[b][1] >= 1.5, errs
