@@ -305,7 +305,8 @@ adlbr_status adlbr_mse_grad(const float *y, const float *t, int64_t n, float *gy
                             double *loss_out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * Coherence-enhancing diffusion (Sec. 4.4, Eq. parabolique), 2D, FP32.
+ * Coherence-enhancing diffusion (Sec. 4.4, Eq. parabolique; in 3D as in the
+ * 3D experiments of Sec. 5), FP32.
  * ------------------------------------------------------------------------ */
 
 /* Bytes of scratch for adlbr_ced_tensor / adlbr_ced_step on grid g. */
@@ -321,9 +322,15 @@ size_t adlbr_ced_scratch_bytes(const adlbr_grid *g);
  * reflected about its border (u(-1) = u(0)) for the convolutions and for the
  * centred-difference gradient.
  *
- *  g        2D grid.
+ * In 3D, J_rho has six channels and eigenvalues mu1 >= mu2 >= mu3; D keeps
+ * its eigenvectors with lambda1 = alpha, lambda2 = alpha + (1 - alpha)
+ * exp(-C / (mu1 - mu2)^2), lambda3 = alpha + (1 - alpha) exp(-C / (mu1 -
+ * mu3)^2) (eigen-decomposition by Jacobi rotations in FP32).
+ *
+ *  g        2D or 3D grid.
  *  u        device float [N].
- *  D        device float [3][N]: planes Dxx, Dxy, Dyy (build_stencils input).
+ *  D        device float [3][N]: planes Dxx, Dxy, Dyy (2D), or [6][N]: Dxx, Dyy,
+ *           Dzz, Dxy, Dxz, Dyz (3D) -- the build_stencils input.
  *  scratch  device, adlbr_ced_scratch_bytes(g) bytes.
  */
 adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, double sigma,

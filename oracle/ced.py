@@ -81,3 +81,54 @@ def tensor_from_J(Jxx, Jxy, Jyy, alpha, C):
 def ced_tensor(u, sigma, rho, alpha, C):
     """The full tensor stage (i) of Sec. 4.4: returns (Dxx, Dxy, Dyy)."""
     return tensor_from_J(*structure_tensor(u, sigma, rho), alpha, C)
+
+
+# ---------------------------------------------------------------- 3D (Sec. 5, 3D experiments)
+# The 3D coherence-enhancing tensor: u_sigma, J_rho as above over three axes
+# (six channels xx, yy, zz, xy, xz, yz); D(J) has the eigenvectors of J and,
+# for eigenvalues mu1 >= mu2 >= mu3 of J, the eigenvalues
+# lambda1 = alpha, lambda2 = alpha + (1 - alpha) exp(-C / (mu1 - mu2)^2),
+# lambda3 = alpha + (1 - alpha) exp(-C / (mu1 - mu3)^2)   (exp(-C/0) = 0).
+# Arrays are indexed [z, y, x]; D is returned as the planes
+# (Dxx, Dyy, Dzz, Dxy, Dxz, Dyz) of the 3D stencil construction.
+
+def blur3(a, s):
+    """Separable Gaussian of standard deviation s over the three axes (x, y, z)."""
+    return blur1d(blur1d(blur1d(np.asarray(a, np.float64), s, -1), s, -2), s, -3)
+
+
+def gradient3(a):
+    """Centred differences with a reflected border; returns (gx, gy, gz)."""
+    ap = np.pad(np.asarray(a, np.float64), 1, mode="symmetric")
+    gx = 0.5 * (ap[1:-1, 1:-1, 2:] - ap[1:-1, 1:-1, :-2])
+    gy = 0.5 * (ap[1:-1, 2:, 1:-1] - ap[1:-1, :-2, 1:-1])
+    gz = 0.5 * (ap[2:, 1:-1, 1:-1] - ap[:-2, 1:-1, 1:-1])
+    return gx, gy, gz
+
+
+def structure_tensor3(u, sigma, rho):
+    """(Jxx, Jyy, Jzz, Jxy, Jxz, Jyz)."""
+    gx, gy, gz = gradient3(blur3(u, sigma))
+    return tuple(blur3(p, rho) for p in (gx * gx, gy * gy, gz * gz, gx * gy, gx * gz, gy * gz))
+
+
+def tensor_from_J3(J, alpha, C):
+    """D(J) from the eigen-decomposition of J (numpy's symmetric solver)."""
+    Jxx, Jyy, Jzz, Jxy, Jxz, Jyz = (np.asarray(a, np.float64) for a in J)
+    M = np.stack([np.stack([Jxx, Jxy, Jxz], -1), np.stack([Jxy, Jyy, Jyz], -1),
+                  np.stack([Jxz, Jyz, Jzz], -1)], -2)
+    mu, V = np.linalg.eigh(M)                      # ascending: mu[..., 2] = mu1
+    d12 = mu[..., 2] - mu[..., 1]
+    d13 = mu[..., 2] - mu[..., 0]
+
+    def lam(d):
+        pos = d > 0
+        return np.where(pos, alpha + (1.0 - alpha) * np.exp(-C / np.where(pos, d * d, 1.0)), alpha)
+
+    L = np.stack([lam(d13), lam(d12), np.full_like(d12, alpha)], -1)   # on v3, v2, v1
+    D = np.einsum("...ik,...k,...jk->...ij", V, L, V)
+    return D[..., 0, 0], D[..., 1, 1], D[..., 2, 2], D[..., 0, 1], D[..., 0, 2], D[..., 1, 2]
+
+
+def ced_tensor3(u, sigma, rho, alpha, C):
+    return np.stack(tensor_from_J3(structure_tensor3(u, sigma, rho), alpha, C))

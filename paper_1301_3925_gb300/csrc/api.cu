@@ -219,18 +219,27 @@ adlbr_status adlbr_mse_grad(const float *y, const float *t, int64_t n, float *gy
     return mse_grad(y, t, n, gy, loss_out, stream);
 }
 
+// CED scratch: tensor temporaries, then D (3 or 6 planes), then the explicit
+// step's accumulator (N floats).
+static size_t ced_temp_bytes(const adlbr_grid *g, int64_t N) {
+    return g->dim == 2 ? ced_tensor_scratch_bytes(N) : ced_tensor3d_scratch_bytes(N);
+}
+static int ced_planes(const adlbr_grid *g) { return g->dim == 2 ? 3 : 6; }
+
 size_t adlbr_ced_scratch_bytes(const adlbr_grid *g) {
-    if (!valid_grid(g) || g->dim != 2) return 0;
+    if (!valid_grid(g)) return 0;
     const int64_t N = npoints(g);
-    // tensor temporaries (6N) + D (3N) + step accumulator (N), floats
-    return ced_tensor_scratch_bytes(N) + (size_t)N * sizeof(float) * 4;
+    return ced_temp_bytes(g, N) + (size_t)N * sizeof(float) * (ced_planes(g) + 1);
 }
 
 adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, double sigma,
                               double rho, double alpha, double C, void *scratch,
                               cudaStream_t stream) {
-    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !D || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    if (g->dim == 3)
+        return launch_ced_tensor3d((int)g->n[0], (int)g->n[1], (int)g->n[2], u, D, sigma, rho, alpha, C,
+                                   scratch, stream);
     return launch_ced_tensor((int)g->n[0], (int)g->n[1], u, D, sigma, rho, alpha, C, scratch, stream);
 }
 
@@ -238,12 +247,12 @@ adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const f
                                 void *scratch, double sigma, double rho, double alpha, double C,
                                 adlbr_dtype w_t, cudaStream_t stream) {
     if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
-    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
     if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
         return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
     const int64_t N = npoints(g);
-    float *D = (float *)((char *)scratch + ced_tensor_scratch_bytes(N));
+    float *D = (float *)((char *)scratch + ced_temp_bytes(g, N));
     const bool fresh = *s == nullptr;
     if (adlbr_status st = acquire_handle(g, w_t, s)) return st;
     adlbr_status st = launch_ced_build(*s, u, sigma, rho, alpha, C, scratch, D, stream);
@@ -258,18 +267,18 @@ adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, v
                             double sigma, double rho, double alpha, double C, double dt,
                             int nsteps, adlbr_dtype w_t, cudaStream_t stream) {
     if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
-    if (!valid_grid(g) || g->dim != 2) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D grid");
+    if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
     if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
     const int64_t N = npoints(g);
-    float *D = (float *)((char *)scratch + ced_tensor_scratch_bytes(N));
-    float *acc = D + 3 * N;
+    float *D = (float *)((char *)scratch + ced_temp_bytes(g, N));
+    float *acc = D + ced_planes(g) * N;
     if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
         return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
     const bool fresh = *s == nullptr;
     if (adlbr_status st = acquire_handle(g, w_t, s)) return st;
     for (int k = 0; k < nsteps; ++k) {
-        // tensor stage fused with the stencil construction (D kept on chip)
+        // tensor stage, stencil construction, one explicit step
         adlbr_status st = launch_ced_build(*s, u, sigma, rho, alpha, C, scratch, D, stream);
         if (st == ADLBR_OK) st = adlbr_step_explicit(*s, u, acc, ADLBR_F32, dt, 1, stream);
         if (st != ADLBR_OK) {

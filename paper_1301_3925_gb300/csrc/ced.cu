@@ -469,6 +469,12 @@ adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double 
 
 adlbr_status launch_ced_build(adlbr_stencils *s, const float *u, double sigma, double rho,
                               double alpha, double C, void *scratch, float *Dtmp, cudaStream_t st) {
+    if (s->dim == 3) {
+        if (adlbr_status e = launch_ced_tensor3d((int)s->n[0], (int)s->n[1], (int)s->n[2], u, Dtmp, sigma, rho,
+                                                 alpha, C, scratch, st))
+            return e;
+        return launch_build3d(s, Dtmp, ADLBR_F32, st);
+    }
     if (adlbr_status e = launch_ced_tensor((int)s->n[0], (int)s->n[1], u, Dtmp, sigma, rho, alpha, C,
                                            scratch, st))
         return e;

@@ -168,6 +168,17 @@ def restoration_problem(N, kappa, alpha=1.0 / 3.0):
     return D, (Yf < 0.5).astype(np.float64), Yf
 
 
+def radial3d(n, seed, R=0.5, noise_var=0.5):
+    """The synthetic 3D image of the paper's 3D experiments on the n^3
+    cell-centred grid of [0,1]^3: u0 = cos(2 (r/R)^3) with r = |x|, and
+    u0 + Gaussian noise of variance noise_var.  Returns (u0, noisy), [z, y, x]."""
+    c = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    u0 = np.cos(2.0 * (r / R) ** 3)
+    return u0, u0 + rng(seed).normal(0.0, np.sqrt(noise_var), u0.shape)
+
+
 def batch_items(seed=100, n_images=64, n_volumes=8, img_sides=(256, 2048), vol_sides=(64, 192),
                 kappa=(5.0, 100.0)):
     """Uneven batch: per item a dict with its shape, tensor-field seed and
