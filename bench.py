@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-implicit", action="store_true", help="skip the implicit-step measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D measurement and precision study")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-step measurement")
+    p.add_argument("--no-ced3d", action="store_true", help="skip the 3D CED measurement")
     p.add_argument("--precision-steps", type=int, default=100)
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
@@ -318,6 +319,51 @@ def batch_measurement(peak, steps=20):
     finally:
         for h in hs:
             ab.adlbr_stencils_destroy(h)
+
+
+def ced3d_measurement(steps=20):
+    """The 3D coherence-enhancing experiment: 100^3 radial image cos(2 (r/R)^3)
+    plus Gaussian noise of variance 0.5 (seed 8), sigma 0.5, rho 4, alpha 1e-2,
+    C 1e-5, `steps` steps of dt = 1e-3 on [0,1]^3 (dt = 10 in grid units, so
+    implicit steps): tensor, stencils (F32 weights), CG to 1e-6."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    n = 100
+    dt = 1e-3 * n * n
+    u0, noisy = synth.radial3d(n, 8)
+    g = ab.grid((n, n, n))
+    u = torch.from_numpy(noisy.astype(np.float32).ravel()).cuda()
+    x = torch.empty_like(u)
+    scratch = torch.empty(ab.adlbr_ced_scratch_bytes(g), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    h = None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_tensor, t_solve, iters = [], [], []
+    try:
+        for _ in range(steps):
+            ev[0].record(st)
+            h = ab.adlbr_ced_stencils(h, g, u, scratch, 0.5, 4.0, 1e-2, 1e-5, ab.F32)
+            ev[1].record(st)
+            x.copy_(u)
+            it, _ = ab.adlbr_step_implicit(h, u, x, dt, 1e-6, 4000)
+            u.copy_(x)
+            ev[2].record(st)
+            torch.cuda.synchronize()
+            t_tensor.append(ev[0].elapsed_time(ev[1]))
+            t_solve.append(ev[1].elapsed_time(ev[2]))
+            iters.append(it)
+    finally:
+        if h:
+            ab.adlbr_stencils_destroy(h)
+    ug = u.double().cpu().numpy().reshape(n, n, n)
+    rms = lambda a: float(np.sqrt(np.mean(a ** 2)))
+    ms = float(np.mean(t_tensor) + np.mean(t_solve))
+    return {"grid": [n, n, n], "steps": steps, "dt_grid_units": dt,
+            "ms_per_step": ms, "tensor_and_stencils_ms": float(np.mean(t_tensor)),
+            "implicit_ms": float(np.mean(t_solve)), "cg_iters_mean": float(np.mean(iters)),
+            "gpts_per_step": n ** 3 / (ms * 1e-3) / 1e9,
+            "rms_to_clean": {"noisy": rms(noisy - u0), "result": rms(ug - u0)}}
 
 
 def volume_measurement(peak, steps):
@@ -607,6 +653,7 @@ def main():
     implicit = None if args.no_implicit or rank != 0 else implicit_measurement(peak)
     volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)
     batch = None if args.no_batch or rank != 0 else batch_measurement(peak)
+    ced3d = None if args.no_ced3d or rank != 0 else ced3d_measurement()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -625,7 +672,8 @@ def main():
                 "stages_ms": {"tensor": st_tensor, "build": st_build, "explicit_step": st_step},
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
-                "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch}
+                "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch,
+                "ced3d": ced3d}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:

@@ -194,3 +194,37 @@ def test_apply3d_full_size_sampled():
         ow = gw[z0:z1, y0:y1, x0:x1].reshape(-1, 6)
         ref = oracle.apply(cs, oracle.NEUMANN, oo, ow, useen[z0:z1, y0:y1, x0:x1])
         assert abs(Au[z, y, x] - ref[z - z0, y - y0, x - x0]) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_fourier_modes_are_eigenvectors(dim):
+    """Constant D on a periodic grid: the Fourier mode cos(xi . z) is an
+    eigenvector of A with eigenvalue sigma(xi) = sum over the stencil V (both
+    signs of every offset) of 2 gamma(e) (1 - cos(xi . e)), i.e. four times
+    the sum over the stored half-stencil (the symbol of the scheme; Fig.
+    Eigen of the paper studies it), on the GPU operator in FP64."""
+    t = torch()
+    if dim == 2:
+        shape = (48, 64)
+        D1 = synth.D_from_angle(np.array(0.37), np.array(7.0))
+    else:
+        shape = (16, 20, 24)
+        D1 = synth.random_spd3(1, 9, kappa_max=6.0)[:, 0]
+    Dfield = np.broadcast_to(D1.reshape(-1, *([1] * dim)), (D1.shape[0],) + shape).copy()
+    h, seen, _ = build(Dfield, shape, t.float64, ab.F64, ab.PERIODIC)
+    try:
+        oo, ow = export(h, shape, ab.F64)
+        k = (3, 5) if dim == 2 else (2, 3, 1)
+        grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")   # [z, y, x] order
+        xi = [2 * np.pi * k[i] / shape[i] for i in range(dim)]
+        phase = sum(xi[i] * grids[i] for i in range(dim))
+        u = np.cos(phase)
+        Au, _ = _gpu_apply(h, u, t.float64)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    # symbol from the (constant) stencil of point 0; offsets are (x, y[, z])
+    e = oo[0]
+    xi_xyz = xi[::-1]
+    sig = sum(4 * ow[0, j] * (1 - np.cos(sum(xi_xyz[c] * e[j, c] for c in range(dim))))
+              for j in range(e.shape[0]))
+    assert np.abs(Au - sig * u).max() <= 1e-12 * max(1.0, sig)
