@@ -34,6 +34,11 @@ UNIT = "Gpts/s"
 N_SIDE = 4096
 CED = dict(sigma=1.0, rho=4.0, alpha=1e-4, C=1e-5, dt=0.02)
 SEED = 1
+# Algorithmic FP32 operations per point of the fused tensor stage (an FMA
+# counts once): sigma blurs 2 x 7, gradient and products 7, rho blurs
+# 2 x 3 x 25, eigen epilogue 20; and the FP32 issue peak it is held against.
+ALU_OPS_PER_POINT = 2 * 7 + 7 + 2 * 3 * 25 + 20
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch at 4096^2, from ncu captures of the
 # current kernels (the summaries under profiles/ give the commands)
 TRAFFIC_4096 = {"ced_fused_kernel": 67.16e6 + 140.92e6, "build2d_kernel": 201.44e6 + 229.27e6,
@@ -572,23 +577,28 @@ def main():
     ms_step = total_ms / K
     value = job_value(ws, N, ms_step)
 
-    # roofline of the dominant kernel (algorithmic bytes per point of each)
+    # roofline of the dominant kernel; the others beside it
     peak, peak_src = measured_peaks()
-    stages = {
-        # u in; D (3 x f32) out
-        "ced_fused_kernel": (st_tensor, 4 + 12),
-        # D in; offsets (int16 x 4) + weights (4 x f16) out
-        "build2d_kernel": (st_build, 12 + 8 + 8),
-        # operator + finalize: u in, stencil in, u out
-        "explicit_step": (st_step, 4 + 16 + 4),
-    }
-    dom = max(stages, key=lambda k: stages[k][0])
-    dom_ms, dom_bpp = stages[dom]
-    achieved = dom_bpp * N / (dom_ms * 1e-3) / 1e9
-    traffic = TRAFFIC_4096.get(dom)
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "bytes_per_point": dom_bpp, "units_per_launch": N}
+
+    def roof_of(name, ms):
+        if name == "ced_fused_kernel":
+            # issue-bound FP32 arithmetic: algorithmic FP32 operations per point
+            # (an FMA counts once) against the FP32 issue rate of the GPU
+            a = ALU_OPS_PER_POINT * N / (ms * 1e-3) / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": a, "peak": FP32_PEAK_TOPS, "unit": "Tops/s",
+                    "frac": a / FP32_PEAK_TOPS, "traffic": TRAFFIC_4096.get(name),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                    "ops_per_point": ALU_OPS_PER_POINT, "units_per_launch": N}
+        bpp = {"build2d_kernel": 12 + 8 + 8, "explicit_step": 4 + 16 + 4}[name]
+        a = bpp * N / (ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                "traffic": TRAFFIC_4096.get(name), "peak_source": peak_src, "bytes_per_point": bpp,
+                "units_per_launch": N}
+
+    stage_ms = {"ced_fused_kernel": st_tensor, "build2d_kernel": st_build, "explicit_step": st_step}
+    dom = max(stage_ms, key=stage_ms.get)
+    roof = roof_of(dom, stage_ms[dom])
+    roof["others"] = [roof_of(k, v) for k, v in stage_ms.items() if k != dom]
     step_gbs = 24 * N / (st_step * 1e-3) / 1e9
 
     # the operator alone on the step's stencils (adlbr_apply: zero Au, accumulate)
