@@ -44,7 +44,8 @@ typedef enum {
     ADLBR_E_ARG = 1,           /* null pointer, bad enum, bad scalar */
     ADLBR_E_SHAPE = 2,         /* bad grid extents or mismatched handles */
     ADLBR_E_NOT_SPD = 3,       /* some D(z) is not symmetric positive definite */
-    ADLBR_E_NONFINITE = 4,     /* some D(z) has a NaN or infinite entry */
+    ADLBR_E_NONFINITE = 4,     /* some D(z) has a NaN or infinite entry, or a
+                                  solver's residual became non-finite */
     ADLBR_E_NOT_CONVERGED = 5, /* iteration limit reached (CG, reduction) */
     ADLBR_E_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     ADLBR_E_CUDA = 7,          /* a CUDA runtime call failed */
@@ -202,7 +203,10 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  *  rhs         device float [N].
  *  x           device float [N]: initial guess on entry, solution on exit.
  *  precond     0: plain CG.  1: flexible CG preconditioned by the U-Net of
- *              adlbr_unet_* with parameters nn (see below).  Plain CG is its
+ *              adlbr_unet_* with parameters nn (see below): z = r/d + gamma c,
+ *              c the network's coarse correction, gamma its Galerkin step
+ *              length <c, r - (I + dt A) r/d> / <c, (I + dt A) c> (two operator
+ *              applications per iteration).  Plain CG is its
  *              fallback: when the preconditioned recursive residual grows
  *              tenfold above its best value or does not halve within 100
  *              iterations, the solve restarts from the initial guess with
@@ -213,7 +217,8 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  *  relres_out  final true relative residual |rhs - (I + dt A) x| / |rhs|.
  * The first call on a handle allocates its solver workspace (cudaMalloc);
  * later calls reuse it.  Synchronises the stream every few iterations.
- * Returns ADLBR_E_NOT_CONVERGED if maxit is reached first.
+ * Returns ADLBR_E_NOT_CONVERGED if maxit is reached first and
+ * ADLBR_E_NONFINITE if the residual becomes non-finite (e.g. a NaN in rhs).
  */
 adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, double dt,
                                  double rtol, int maxit, int precond, const void *nn,

@@ -32,7 +32,7 @@ constexpr int RB = 1216;  // blocks of the vector kernels (8 per SM on 152 SMs)
 
 struct CgState {
     double rr, rr_new, pq, alpha, beta, bb, tol2;
-    int conv, iters, max_iters;  // conv: 0 running, 1 converged, 2 iteration limit
+    int conv, iters, max_iters;  // conv: 0 running, 1 converged, 2 iteration limit, 3 non-finite
     unsigned int count;          // last-block ticket
 };
 
@@ -113,7 +113,9 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
         S->beta = tot / S->rr;
         S->rr = tot;
         S->iters += 1;
-        if (tot <= S->tol2 * S->bb || !(tot == tot))
+        if (!(tot == tot) || tot > 3.0e38)
+            S->conv = 3;   // non-finite residual: stop, reported as a failure
+        else if (tot <= S->tol2 * S->bb)
             S->conv = 1;
         else if (S->iters >= S->max_iters)
             S->conv = 2;
@@ -209,6 +211,10 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
         ADLBR_CUDA(cudaMemcpyAsync(W.q, W.p, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
+        if (!std::isfinite(host.bb) || !std::isfinite(host.rr_new)) {
+            if (iters_out) *iters_out = total_iters;
+            return fail(ADLBR_E_NONFINITE, "non-finite right-hand side or iterate in CG");
+        }
         relres = host.bb > 0 ? std::sqrt(host.rr_new / host.bb) : 0.0;
         // stop when the true residual meets rtol, when refinement stopped
         // paying (x is FP32: the true residual floors near eps32 |I + dt A|),
@@ -250,6 +256,10 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
         }
         total_iters += host.iters;
         cg_converged = host.conv == 1;
+        if (host.conv == 3) {
+            if (iters_out) *iters_out = total_iters;
+            return fail(ADLBR_E_NONFINITE, "CG residual became non-finite after %d iterations", total_iters);
+        }
     }
     if (iters_out) *iters_out = total_iters;
     if (relres_out) *relres_out = relres;

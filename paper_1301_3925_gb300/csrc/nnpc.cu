@@ -31,7 +31,7 @@ constexpr int NF = NR + NS;           // network input channels
 constexpr int NB = 1216;     // blocks of the vector kernels
 
 struct FcgState {
-    double rr, bb, tol2, rz, pq, alpha, beta, s;
+    double rr, bb, tol2, rz, pq, alpha, beta, s, gamma;
     int conv, iters, max_iters;
     unsigned int count;
 };
@@ -213,8 +213,9 @@ __global__ void __launch_bounds__(RT) fcg_init_kernel(int64_t N, const float *__
     }
 }
 
-// z = r / d + s P(y) ; first: rz = <r,z>, p = q = z.  Otherwise: beta =
-// (<r,z> - <r_old,z>) / rz, rz = <r,z> (p updated by fcg_p_kernel).
+// The preconditioner alone (adlbr_nn_precondition): z = r / d + s P(y),
+// with rz = <r,z> and p = q = z (the solver uses the Galerkin-step kernels
+// below instead).
 template <bool FIRST>
 __global__ void __launch_bounds__(RT) fcg_z_kernel(int nx, int64_t N, const float *__restrict__ r,
                                                    const float *__restrict__ r_old,
@@ -245,6 +246,100 @@ __global__ void __launch_bounds__(RT) fcg_z_kernel(int nx, int64_t N, const floa
             S->beta = (tot - oz) / S->rz;
         }
         S->rz = tot;
+    }
+}
+
+// Step length of the network correction (flexible CG with a Galerkin step):
+// the preconditioned residual is z = r/d + gamma c with c = s P(y), and gamma
+// minimises the (I + dt A)-energy of the error of z as an approximation of
+// (I + dt A)^{-1} r:  gamma = <c, r - (I + dt A) r/d> / <c, (I + dt A) c>.
+// With c = 0 (no correction) gamma = 0 and z is the Jacobi step.
+//
+// w = r/d into z, c = s P(y), and the starting values g1 = w, g2 = c of the
+// two operator accumulations.
+__global__ void __launch_bounds__(RT) fcg_w_kernel(int nx, int64_t N, const float *__restrict__ r,
+                                                   const float *__restrict__ d, const float *__restrict__ y,
+                                                   float *__restrict__ w, float *__restrict__ c,
+                                                   float *__restrict__ g1, float *__restrict__ g2,
+                                                   const FcgState *S) {
+    if (S->conv) return;
+    const int Wc = nx / RF;
+    const float s = (float)sqrt(S->rr / (double)N);
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const int xx = (int)(i % nx), yy = (int)(i / nx);
+        const float wi = r[i] / d[i];
+        const float ci = s * y[(int64_t)(yy / RF) * Wc + xx / RF];
+        w[i] = wi;
+        g1[i] = wi;
+        c[i] = ci;
+        g2[i] = ci;
+    }
+}
+
+// gamma = <c, r - g1> / <c, g2>   (g1 = (I + dt A) r/d, g2 = (I + dt A) c)
+__global__ void __launch_bounds__(RT) fcg_gamma_kernel(int64_t N, const float *__restrict__ r,
+                                                       const float *__restrict__ c, const float *__restrict__ g1,
+                                                       const float *__restrict__ g2, double *partials,
+                                                       double *partials2, FcgState *S) {
+    if (S->conv) return;
+    FFAcc sn, sm;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        ff_add_prod(sn, c[i], r[i] - g1[i]);
+        ff_add_prod(sm, c[i], g2[i]);
+    }
+    const double pn = block_sum_ff(sn);
+    const double pm = block_sum_ff(sm);
+    if (threadIdx.x == 0) partials2[blockIdx.x] = pm;
+    double tot;
+    if (finish_reduction(pn, partials, &S->count, tot)) {
+        double m = 0.0;
+        for (int k = 0; k < (int)gridDim.x; ++k) m += ((volatile double *)partials2)[k];
+        S->gamma = m > 0.0 ? tot / m : 0.0;
+    }
+}
+
+// z = w + gamma c (in place over w), Az = g1 + gamma g2 (in place over g1);
+// first: rz = <r,z>.  Otherwise: beta = (<r,z> - <r_old,z>) / rz, rz = <r,z>.
+template <bool FIRST>
+__global__ void __launch_bounds__(RT) fcg_z2_kernel(int64_t N, const float *__restrict__ r,
+                                                    const float *__restrict__ r_old, float *__restrict__ z,
+                                                    const float *__restrict__ c, float *__restrict__ g1,
+                                                    const float *__restrict__ g2, double *partials,
+                                                    double *partials2, FcgState *S) {
+    if (S->conv) return;
+    const float gamma = (float)S->gamma;
+    FFAcc s_rz, s_oz;
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const float zi = fmaf(gamma, c[i], z[i]);
+        z[i] = zi;
+        g1[i] = fmaf(gamma, g2[i], g1[i]);
+        ff_add_prod(s_rz, r[i], zi);
+        if (!FIRST) ff_add_prod(s_oz, r_old[i], zi);
+    }
+    const double prz = block_sum_ff(s_rz);
+    const double poz = block_sum_ff(s_oz);
+    if (threadIdx.x == 0) partials2[blockIdx.x] = poz;
+    double tot;
+    if (finish_reduction(prz, partials, &S->count, tot)) {
+        if (!FIRST) {
+            double oz = 0.0;
+            for (int k = 0; k < (int)gridDim.x; ++k) oz += ((volatile double *)partials2)[k];
+            S->beta = (tot - oz) / S->rz;
+        }
+        S->rz = tot;
+    }
+}
+
+// p = z + beta p ; q = Az + beta q   (first: p = z, q = Az)
+template <bool FIRST>
+__global__ void fcg_p2_kernel(int64_t N, const float *__restrict__ z, const float *__restrict__ Az,
+                              float *__restrict__ p, float *__restrict__ q, const FcgState *S) {
+    if (S->conv) return;
+    const float beta = FIRST ? 0.f : (float)S->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        p[i] = FIRST ? z[i] : fmaf(beta, p[i], z[i]);
+        q[i] = FIRST ? Az[i] : fmaf(beta, q[i], Az[i]);
     }
 }
 
@@ -284,25 +379,15 @@ __global__ void __launch_bounds__(RT) fcg_x_kernel(int64_t N, float *__restrict_
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->rr = tot;
         S->iters += 1;
-        if (tot <= S->tol2 * S->bb || !(tot == tot))
+        if (!(tot == tot) || tot > 3.0e38)
+            S->conv = 3;   // non-finite residual: stop, reported as a failure
+        else if (tot <= S->tol2 * S->bb)
             S->conv = 1;
         else if (S->iters >= S->max_iters)
             S->conv = 2;
     }
 }
 
-// p <- z + beta p ; q <- p
-__global__ void fcg_p_kernel(int64_t N, const float *__restrict__ z, float *__restrict__ p,
-                             float *__restrict__ q, const FcgState *S) {
-    if (S->conv) return;
-    const float beta = (float)S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float pi = z[i] + beta * p[i];
-        p[i] = pi;
-        q[i] = pi;
-    }
-}
 
 // training target: R((xs - x - r / d) / s) with s = rms(r) (given)
 __global__ void target_kernel(int nx, int ny, const float *__restrict__ xs, const float *__restrict__ x,
@@ -357,6 +442,7 @@ __global__ void __launch_bounds__(RT) sumsq_kernel(int64_t N, const float *__res
 
 struct NnWorkspace {
     float *r, *p, *q, *z, *r_old, *d, *feat, *y, *xs;
+    float *c, *g1, *g2;   // network correction, (I + dt A) r/d, (I + dt A) c
     double *partials, *partials2, *scal;
     FcgState *S;
     unsigned *dmax, *cnt;
@@ -368,7 +454,7 @@ struct NnWorkspace {
 
 static adlbr_status nn_workspace(adlbr_stencils *s, NnWorkspace &W) {
     const int64_t N = s->N, Nc = N / (RF * RF);
-    size_t need = (7 * (size_t)N + (NF + 1) * (size_t)Nc) * sizeof(float) + 3 * NB * sizeof(double) + 4096;
+    size_t need = (10 * (size_t)N + (NF + 1) * (size_t)Nc) * sizeof(float) + 3 * NB * sizeof(double) + 4096;
     if (!s->ws_nn || s->ws_nn_bytes < need) {
         if (s->ws_nn) cudaFree(s->ws_nn);
         s->ws_nn = nullptr;
@@ -383,7 +469,10 @@ static adlbr_status nn_workspace(adlbr_stencils *s, NnWorkspace &W) {
     W.r_old = W.z + N;
     W.d = W.r_old + N;
     W.xs = W.d + N;
-    W.feat = W.xs + N;
+    W.c = W.xs + N;
+    W.g1 = W.c + N;
+    W.g2 = W.g1 + N;
+    W.feat = W.g2 + N;
     W.y = W.feat + NF * Nc;
     uintptr_t a = (uintptr_t)(W.y + Nc);
     a = (a + 255) & ~(uintptr_t)255;
@@ -477,8 +566,32 @@ adlbr_status run_fcg(adlbr_stencils *s, const float *b, float *x, double dt, dou
     return run_fcg_hooked(s, b, x, dt, rtol, maxit, nn, iters_out, relres_out, 2, nullptr, nullptr, st);
 }
 
-// Flexible PCG; when hook != NULL it is called with the current residual and
-// iterate every `every` iterations while the solve runs.
+// The next search direction of the flexible solve: network correction, its
+// Galerkin step length, z and (I + dt A) z, then p and q = (I + dt A) p.
+template <bool FIRST>
+static adlbr_status galerkin_direction(adlbr_stencils *s, NnWorkspace &W, adlbr_unet *net, const float *params,
+                                       double dt, const int *skip, cudaStream_t st) {
+    const int nx = (int)s->n[0], ny = (int)s->n[1];
+    const int64_t N = s->N;
+    dim3 gc(blocks_for(nx / RF, 128), (unsigned)(ny / RF));
+    coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, W.feat);
+    if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
+    fcg_w_kernel<<<NB, RT, 0, st>>>(nx, N, W.r, W.d, W.y, W.z, W.c, W.g1, W.g2, W.S);
+    if (adlbr_status e = launch_accumulate(s, W.z, W.g1, ADLBR_F32, dt, skip, st)) return e;
+    if (adlbr_status e = launch_accumulate(s, W.c, W.g2, ADLBR_F32, dt, skip, st)) return e;
+    fcg_gamma_kernel<<<NB, RT, 0, st>>>(N, W.r, W.c, W.g1, W.g2, W.partials, W.partials2, W.S);
+    fcg_z2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.r, W.r_old, W.z, W.c, W.g1, W.g2, W.partials, W.partials2,
+                                            W.S);
+    fcg_p2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.z, W.g1, W.p, W.q, W.S);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+// Flexible PCG (Polak-Ribiere beta) with the Galerkin-step preconditioner:
+// per iteration two operator applications (to r/d and to the correction c)
+// and no other; q = (I + dt A) p follows from them by linearity.  When hook
+// != NULL it is called with the current residual and iterate every `every`
+// iterations while the solve runs.
 static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
                                    int maxit, const adlbr_nn_precond *nn, int *iters_out,
                                    double *relres_out, int every, CgHook hook, void *ctx,
@@ -498,8 +611,8 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     if (adlbr_status e = launch_accumulate(s, x, W.q, ADLBR_F32, dt, nullptr, st)) return e;
     fcg_init_kernel<<<NB, RT, 0, st>>>(N, b, x, W.q, W.r, W.partials, W.partials2, W.S);
     ADLBR_CUDA(cudaGetLastError());
-    if (adlbr_status e = precondition<true>(s, W, nn->net, nn->params, st)) return e;
     const int *skip = (const int *)((const char *)W.S + offsetof(FcgState, conv));
+    if (adlbr_status e = galerkin_direction<true>(s, W, nn->net, nn->params, dt, skip, st)) return e;
     FcgState host = {};
     const int chunk = every > 0 ? every : 2;
     int it = 0;
@@ -519,16 +632,19 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
         if (hook)
             if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
         for (int k = 0; k < chunk; ++k) {
-            if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, skip, st)) return e;
+            // q = (I + dt A) p is carried by the recurrences: no operator here
             fcg_q_kernel<<<NB, RT, 0, st>>>(N, W.p, W.q, W.partials, W.S);
             fcg_x_kernel<<<NB, RT, 0, st>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
-            if (adlbr_status e = precondition<false>(s, W, nn->net, nn->params, st)) return e;
-            fcg_p_kernel<<<NB, RT, 0, st>>>(N, W.z, W.p, W.q, W.S);
+            if (adlbr_status e = galerkin_direction<false>(s, W, nn->net, nn->params, dt, skip, st)) return e;
         }
         ADLBR_CUDA(cudaGetLastError());
         it += chunk;
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
+        if (host.conv == 3 && !hook) {   // non-finite: the preconditioner failed
+            fall_back = true;
+            break;
+        }
         if (host.conv) break;
         if (!hook) {
             const double rel = host.bb > 0 ? std::sqrt(host.rr / host.bb) : 0.0;
@@ -556,9 +672,14 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     FcgState fin = {};
     ADLBR_CUDA(cudaMemcpyAsync(&fin, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
     ADLBR_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(fin.bb) || !std::isfinite(fin.rr))
+        return fail(ADLBR_E_NONFINITE, "non-finite right-hand side or iterate in the preconditioned solve");
     const double relres = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
     if (iters_out) *iters_out = host.iters;
     if (relres_out) *relres_out = relres;
+    if (host.conv == 3)
+        return fail(ADLBR_E_NONFINITE, "preconditioned CG residual became non-finite after %d iterations",
+                    host.iters);
     if (host.conv != 1)
         return fail(ADLBR_E_NOT_CONVERGED, "preconditioned CG stopped after %d iterations (residual %.3e)",
                     host.iters, relres);

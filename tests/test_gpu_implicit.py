@@ -117,3 +117,22 @@ def test_restoration_against_exact_solution():
     # and falls more slowly there (pre-asymptotic)
     for a, b in ((200, 400), (400, 800)):
         assert errs[a][0] / errs[b][0] >= 1.6 and errs[a][1] / errs[b][1] >= 1.3, errs
+
+
+def test_cg_non_finite_rhs_is_an_error():
+    """A NaN in the right-hand side makes the residual non-finite: the solve
+    stops and reports ADLBR_E_NONFINITE instead of a converged result."""
+    t = torch()
+    shape = (64, 64)
+    D = synth.smooth_field2d(*shape, seed=4, kappa_min=1, kappa_max=20, lattice=8)
+    h, seen, _ = build(D, shape, t.float32, ab.F32)
+    try:
+        bn = synth.u_uniform(shape, 5).ravel()
+        bn[100] = np.nan
+        b = dev(bn, t.float32)
+        x = b.clone()
+        with pytest.raises(ab.AdlbrError) as ei:
+            ab.adlbr_step_implicit(h, b, x, 50.0, 1e-6, 500)
+        assert ei.value.status == 4
+    finally:
+        ab.adlbr_stencils_destroy(h)

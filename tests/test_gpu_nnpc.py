@@ -1,6 +1,7 @@
 """The learned preconditioner (not in the paper): M(r) against the FP64
-oracle, solver-generated training pairs, flexible PCG, and the gain of the
-trained network over plain CG."""
+oracle, solver-generated training pairs, flexible PCG with the Galerkin step
+length, the plain-CG fallback, and the gain of the trained network over the
+solver without it."""
 import numpy as np
 import pytest
 
@@ -104,10 +105,10 @@ def test_trained_preconditioner_report():
     """Trains the network on the solver's own (residual, error) pairs, then
     solves a held-out right-hand side three ways: plain CG, flexible PCG with
     the Jacobi part alone (output layer zeroed) and flexible PCG with the
-    trained network.  Asserted: the training loss falls, the trained PCG
-    reaches the same residual and solution as CG.  The iteration counts are
-    printed; on this problem the trained network does not beat CG (the
-    measured counts are recorded with the design notes)."""
+    trained network (its correction taken with the Galerkin step length).
+    Asserted: the training loss falls, every solve reaches the CG solution,
+    and the trained network needs fewer iterations than the same solver
+    without it (its gain over the method without it)."""
     t = torch()
     shape = (192, 192)
     h, oo, ow, diag, dt = _problem(shape, 11)
@@ -140,16 +141,46 @@ def test_trained_preconditioner_report():
           % (it_cg, its["jacobi"][0], its["trained"][0]))
     for name, (it, rel, d) in its.items():
         assert rel <= 1e-4 and d <= 2e-4, (name, it, rel, d)
+    assert its["trained"][0] < its["jacobi"][0], its
 
 
-def test_bad_network_falls_back_to_cg():
-    """An untrained network with a large output layer spoils the flexible
-    solve; the solver detects it and finishes with plain CG at the same
-    residual (iterations then count both phases)."""
+def test_badly_scaled_network_stays_near_jacobi():
+    """An untrained network with an output layer 50 times too large: the
+    Galerkin step length shrinks its correction, so the solve converges in
+    about the iterations of Jacobi-preconditioned FCG, without the fallback."""
     t = torch()
     shape = (96, 112)
     h, oo, ow, diag, dt = _problem(shape, 3)
-    theta = _params(4, scale_out=50.0)
+    pcs = []
+    try:
+        b = dev(synth.u_uniform(shape, 3).ravel(), t.float32)
+        x1 = b.clone()
+        it_cg, _ = ab.adlbr_step_implicit(h, b, x1, dt, 1e-6, 4000)
+        its = {}
+        for name, scale in (("jacobi", 0.0), ("bad", 50.0)):
+            pcs.append(nn.Preconditioner(dev(_params(4, scale_out=scale), t.float32), shape[1], shape[0]))
+            x2 = b.clone()
+            its[name] = ab.adlbr_step_implicit(h, b, x2, dt, 1e-6, 4000, precond=1, nn=pcs[-1].desc)
+            assert ab.adlbr_last_fallback() == 0
+            assert (x1 - x2).abs().max().item() <= 2e-4
+    finally:
+        for pc in pcs:
+            pc.close()
+        ab.adlbr_stencils_destroy(h)
+    print("CG %d, Jacobi FCG %d, bad-network FCG %d" % (it_cg, its["jacobi"][0], its["bad"][0]))
+    assert its["bad"][0] <= 1.25 * its["jacobi"][0] + 5, its
+    assert its["bad"][1] <= 1e-4
+
+
+def test_non_finite_network_falls_back_to_cg():
+    """A network whose output is not finite (a NaN output bias, made on the
+    host) spoils the flexible solve; the solver detects it and finishes with
+    plain CG at the same residual (iterations then count both phases)."""
+    t = torch()
+    shape = (96, 112)
+    h, oo, ow, diag, dt = _problem(shape, 3)
+    theta = _params(4)
+    theta[-1] = np.nan
     pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0])
     try:
         b = dev(synth.u_uniform(shape, 3).ravel(), t.float32)
@@ -162,7 +193,7 @@ def test_bad_network_falls_back_to_cg():
     finally:
         pc.close()
         ab.adlbr_stencils_destroy(h)
-    print("CG %d, bad-network solve %d (fallback %d)" % (it_cg, it_nn, fb))
+    print("CG %d, non-finite network solve %d (fallback %d)" % (it_cg, it_nn, fb))
     assert fb == 1
-    assert it_nn > it_cg
+    assert it_nn >= it_cg
     assert rel <= 1e-5 and d <= 2e-4, (rel, d)
