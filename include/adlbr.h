@@ -106,7 +106,8 @@ adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtyp
 
 /* Synchronises `stream`, returns the handle's sticky build status
  * (ADLBR_OK, ADLBR_E_NONFINITE, ADLBR_E_NOT_SPD, ADLBR_E_RANGE,
- * ADLBR_E_NOT_CONVERGED) and clears it. */
+ * ADLBR_E_NOT_CONVERGED, or ADLBR_E_TIMEOUT when an operator kernel on this
+ * handle gave up a bounded wait for a tile copy) and clears it. */
 adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream);
 
 /* Grid of a handle. */

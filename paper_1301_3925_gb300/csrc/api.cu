@@ -114,6 +114,7 @@ adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream) {
     if (bits & ERRBIT_NOT_SPD) return fail(ADLBR_E_NOT_SPD, "tensor not positive definite");
     if (bits & ERRBIT_RANGE) return fail(ADLBR_E_RANGE, "stencil offset out of storage range");
     if (bits & ERRBIT_NOT_CONVERGED) return fail(ADLBR_E_NOT_CONVERGED, "reduction did not converge");
+    if (bits & ERRBIT_TIMEOUT) return fail(ADLBR_E_TIMEOUT, "a device-side wait for a tile copy gave up");
     return ADLBR_OK;
 }
 

@@ -23,6 +23,20 @@ using op::red_add;
 using op::Tile;
 using op::wrap;
 
+// FP32 u on a non-periodic grid: the window arrives by one TMA copy.
+template <int TW, int TH, int NT, int WX, bool F16W>
+__global__ void __launch_bounds__(NT) apply2d_tiled_tma(int nx, int ny, int bc, float scale,
+                                                        const short4 *__restrict__ offs,
+                                                        const void *__restrict__ wbase, adlbr_dtype wt,
+                                                        const float *__restrict__ u, float *__restrict__ acc,
+                                                        const int *__restrict__ skip,
+                                                        const __grid_constant__ CUtensorMap map, int *err) {
+    extern __shared__ __align__(128) float smem[];
+    if (skip && *skip) return;
+    op::tile2d<float, TW, TH, NT, WX, F16W, true>(nx, ny, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TW,
+                                                  blockIdx.y * TH, smem, &map, err);
+}
+
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W>
 __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, float scale,
                                                     const short4 *__restrict__ offs,
@@ -220,7 +234,19 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
             using T = Tile<TW, TH, NT, WX>;
             dim3 grid(blocks_for(s->n[0], TW), blocks_for(s->n[1], TH));
             constexpr size_t smem = 2 * T::P * T::WH * sizeof(float);
-            if (s->w_t == ADLBR_F16)
+            CUtensorMap map;
+            if (std::is_same<UT, float>::value && s->bc != ADLBR_PERIODIC &&
+                tma::encode_2d_f32(&map, reinterpret_cast<const float *>(u), (int)s->n[0], (int)s->n[1], T::WW,
+                                   T::WH)) {
+                if (s->w_t == ADLBR_F16)
+                    apply2d_tiled_tma<TW, TH, NT, WX, true><<<grid, NT, smem, st>>>(
+                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w, s->w_t,
+                        reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+                else
+                    apply2d_tiled_tma<TW, TH, NT, WX, false><<<grid, NT, smem, st>>>(
+                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w, s->w_t,
+                        reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+            } else if (s->w_t == ADLBR_F16)
                 apply2d_tiled<UT, TW, TH, NT, WX, true><<<grid, NT, smem, st>>>(
                     (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w,
                     s->w_t, u, acc, skip);

@@ -29,6 +29,7 @@ enum : int {
     ERRBIT_NOT_SPD = 1 << 1,
     ERRBIT_RANGE = 1 << 2,
     ERRBIT_NOT_CONVERGED = 1 << 3,
+    ERRBIT_TIMEOUT = 1 << 4,   // a bounded device-side wait gave up
 };
 
 }  // namespace adlbr

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace adlbr {
 namespace op {
@@ -79,12 +80,16 @@ __device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z,
 
 // acc += scale A u over the tile at (x0, y0); every thread of the block
 // calls it (block-wide barriers inside).  smem: 2 * WH * P floats, 16-byte
-// aligned.
-template <typename UT, int TW, int TH, int NT, int WX, bool F16W>
+// aligned (128-byte for TMA).  TMA: the u window (FP32, non-periodic grid,
+// nx % 4 == 0) arrives as one bulk tensor copy of the map's WW x WH box;
+// cells outside the grid are zero-filled, as the plain staging leaves them.
+// If the bounded wait for the copy gives up, the block records
+// ERRBIT_TIMEOUT in *err and returns.
+template <typename UT, int TW, int TH, int NT, int WX, bool F16W, bool TMA = false>
 __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, const short4 *__restrict__ offs,
                                        const void *__restrict__ wbase, adlbr_dtype wt,
                                        const UT *__restrict__ u, float *__restrict__ acc, int x0, int y0,
-                                       float *smem) {
+                                       float *smem, const CUtensorMap *map = nullptr, int *err = nullptr) {
     using T = Tile<TW, TH, NT, WX>;
     constexpr int WW = T::WW, WH = T::WH, P = T::P;
     float *uw = smem, *aw = smem + WH * P;
@@ -95,6 +100,23 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
     const bool full = x0 + TW <= nx && y0 + TH <= ny;
     const bool inside = periodic || (x0 >= HALO && y0 >= HALO && x0 + TW + HALO <= nx &&
                                      y0 + TH + HALO <= ny);
+    if constexpr (TMA) {
+        static_assert(T::P == WW && std::is_same<UT, float>::value, "TMA box = window rows");
+        __shared__ uint64_t bar;
+        if (threadIdx.x == 0) tma::bar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::bar_expect_tx(&bar, WW * WH * sizeof(float));
+            tma::load_2d(uw, map, x0 - HALO, y0 - HALO, &bar);
+        }
+        for (int c4 = threadIdx.x; c4 < WH * WW / 4; c4 += NT)
+            *reinterpret_cast<float4 *>(&aw[c4 * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = tma::bar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, ERRBIT_TIMEOUT);
+            return;
+        }
+    } else {
     // stage u over the window (4 cells per step), zero the accumulator
     const bool vec = std::is_same<UT, float>::value && (nx % 4) == 0 && !periodic &&
                      ((uintptr_t)u % 16) == 0;
@@ -124,6 +146,7 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
         *reinterpret_cast<float4 *>(&aw[wy * P + wx]) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx = (warp % T::WARPS_X) * WX + lane % WX;
     const int ty = (warp / T::WARPS_X) * T::WR + lane / WX;
