@@ -101,6 +101,19 @@ __global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled(int nx, int ny, int 
                                      blockIdx.y * TY, blockIdx.z * TZ, smem);
 }
 
+template <int TX, int TY, int TZ, bool F16W>
+__global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled_tma(int nx, int ny, int nz, int bc, float scale,
+                                                                const char4 *__restrict__ offs,
+                                                                const void *__restrict__ wbase, adlbr_dtype wt,
+                                                                const float *__restrict__ u, float *__restrict__ acc,
+                                                                const int *__restrict__ skip,
+                                                                const __grid_constant__ CUtensorMap map, int *err) {
+    extern __shared__ __align__(128) float smem[];
+    if (skip && *skip) return;
+    op::tile3d<float, TX, TY, TZ, F16W, true>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
+                                              blockIdx.y * TY, blockIdx.z * TZ, smem, &map, err);
+}
+
 template <typename UT, typename AT = typename UTraits<UT>::acc>
 __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, int bc, AT scale,
                                                        const char4 *__restrict__ offs,
@@ -266,7 +279,20 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
         constexpr size_t smem = 2 * op::Block3<TX, TY, TZ>::CELLS * sizeof(float);
         static_assert(smem <= 48 * 1024, "default shared-memory limit");
         dim3 grid(blocks_for(s->n[0], TX), blocks_for(s->n[1], TY), blocks_for(s->n[2], TZ));
-        if (s->w_t == ADLBR_F16)
+        using B3 = op::Block3<TX, TY, TZ>;
+        CUtensorMap map;
+        if (std::is_same<UT, float>::value && s->bc != ADLBR_PERIODIC &&
+            tma::encode_3d_f32(&map, reinterpret_cast<const float *>(u), (int)s->n[0], (int)s->n[1],
+                               (int)s->n[2], B3::WX, B3::WY, B3::WZ)) {
+            if (s->w_t == ADLBR_F16)
+                apply3d_tiled_tma<TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
+                    (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs, s->w,
+                    s->w_t, reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+            else
+                apply3d_tiled_tma<TX, TY, TZ, false><<<grid, TX * TY, smem, st>>>(
+                    (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs, s->w,
+                    s->w_t, reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+        } else if (s->w_t == ADLBR_F16)
             apply3d_tiled<UT, TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
                 (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
                 s->w, s->w_t, u, acc, skip);

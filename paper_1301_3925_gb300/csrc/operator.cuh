@@ -262,12 +262,15 @@ __device__ __forceinline__ void weights6_f16_scaled(const void *wbase, int64_t z
 }
 
 // acc += scale A u over the block at (x0, y0, z0); all TX * TY threads of
-// the CTA call it.  smem: 2 * Block3::CELLS floats, 16-byte aligned.
-template <typename UT, int TX, int TY, int TZ, bool F16W>
+// the CTA call it.  smem: 2 * Block3::CELLS floats, 16-byte aligned (128 for
+// TMA).  TMA: as in tile2d, the window (a WX x WY x WZ box) arrives by one
+// bulk tensor copy on non-periodic FP32 grids.
+template <typename UT, int TX, int TY, int TZ, bool F16W, bool TMA = false>
 __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float scale,
                                        const char4 *__restrict__ offs, const void *__restrict__ wbase,
                                        adlbr_dtype wt, const UT *__restrict__ u, float *__restrict__ acc,
-                                       int x0, int y0, int z0, float *smem) {
+                                       int x0, int y0, int z0, float *smem, const CUtensorMap *map = nullptr,
+                                       int *err = nullptr) {
     using B = Block3<TX, TY, TZ>;
     constexpr int WY = B::WY, WZ = B::WZ, PX = B::PX, PY = B::PY;
     constexpr int NT = TX * TY;
@@ -278,10 +281,27 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
                                      y0 + TY + H3 <= ny && z0 + TZ + H3 <= nz);
     const int wx0 = x0 - XL;   // grid x of window column 0 (a multiple of 4)
     const int64_t nxy = (int64_t)nx * ny;
+    constexpr int Q = PX / 4;   // float4s per window row
+    if constexpr (TMA) {
+        static_assert(std::is_same<UT, float>::value, "TMA windows are FP32");
+        __shared__ uint64_t bar;
+        if (threadIdx.x == 0) tma::bar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma::bar_expect_tx(&bar, B::CELLS * sizeof(float));
+            tma::load_3d(uw, map, wx0, y0 - H3, z0 - H3, &bar);
+        }
+        for (int c4 = threadIdx.x; c4 < B::CELLS / 4; c4 += NT)
+            *reinterpret_cast<float4 *>(&aw[c4 * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = tma::bar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, ERRBIT_TIMEOUT);
+            return;
+        }
+    } else {
     // stage u (4 cells per step), zero the accumulator
     const bool vec = std::is_same<UT, float>::value && (nx % 4) == 0 && !periodic &&
                      ((uintptr_t)u % 16) == 0;
-    constexpr int Q = PX / 4;   // float4s per window row
     for (int c4 = threadIdx.x; c4 < WZ * WY * Q; c4 += NT) {
         const int wz = c4 / (WY * Q), rem = c4 - wz * (WY * Q);
         const int wy = rem / Q, wx = (rem - wy * Q) * 4;
@@ -312,6 +332,7 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
         *reinterpret_cast<float4 *>(&aw[o]) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
+    }
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x = x0 + tx, y = y0 + ty;
     if (x < nx && y < ny) {

@@ -58,11 +58,14 @@ __device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, int x
         : "memory");
 }
 
-// Host: a 2D FP32 tensor map over a row-major nx x ny array with a box of
-// bx x by elements (zero fill out of bounds).  False when the driver entry
-// point is unavailable or the layout is not encodable (the caller then uses
-// plain loads).
-inline bool encode_2d_f32(CUtensorMap *map, const float *base, int nx, int ny, int bx, int by) {
+__device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+inline PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static bool looked_up = false;
     if (!looked_up) {
@@ -74,6 +77,30 @@ inline bool encode_2d_f32(CUtensorMap *map, const float *base, int nx, int ny, i
             q == cudaDriverEntryPointSuccess)
             encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return encode;
+}
+
+// Host: a 3D FP32 tensor map over an nx x ny x nz array (x fastest) with a
+// box of bx x by x bz elements (zero fill out of bounds).
+inline bool encode_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by, int bz) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
+    if (!encode) return false;
+    if (((uintptr_t)base & 15) || (nx % 4) || bx > 256 || by > 256 || bz > 256 || (bx * 4) % 16) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Host: a 2D FP32 tensor map over a row-major nx x ny array with a box of
+// bx x by elements (zero fill out of bounds).  False when the driver entry
+// point is unavailable or the layout is not encodable (the caller then uses
+// plain loads).
+inline bool encode_2d_f32(CUtensorMap *map, const float *base, int nx, int ny, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
     if (!encode) return false;
     if (((uintptr_t)base & 15) || (nx % 4) || bx > 256 || by > 256 || (bx * 4) % 16) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
