@@ -249,6 +249,16 @@ typedef struct adlbr_unet adlbr_unet; /* opaque: shape and activation buffers */
 adlbr_status adlbr_unet_create(int cin, int c1, int c2, int c3, int batch, int H, int W,
                                adlbr_unet **out);
 adlbr_status adlbr_unet_destroy(adlbr_unet *n);
+
+/* Run this network's forward 3x3 convolutions on the tensor cores (on != 0):
+ * tcgen05 implicit GEMMs with BF16 operands (activations and weights rounded
+ * to BF16, accumulation in FP32; relative output differences to the FP32
+ * forward of order 1e-2), weights repacked (one launch) at every forward
+ * call.  For the inference path (the preconditioner): adlbr_unet_backward
+ * returns ADLBR_E_ARG after a tensor-core forward.  on = 0 returns to the FP32
+ * kernels.  ADLBR_E_SHAPE if a layer has other than 16,
+ * 32 or 64 output channels or more than 160 input channels. */
+adlbr_status adlbr_unet_set_tensor_cores(adlbr_unet *n, int on);
 /* Number of parameters (length of the flat parameter vector). */
 int64_t adlbr_unet_num_params(const adlbr_unet *n);
 /* y [batch][1][H][W] = net(params, x [batch][cin][H][W]); keeps the

@@ -68,6 +68,7 @@ def lib():
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
             "adlbr_last_fallback": (_i32, []),
+            "adlbr_unet_set_tensor_cores": (_i32, [_vp, _i32]),
             "adlbr_batch_create": (_i32, [_i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp), _vp]),
             "adlbr_batch_step": (_i32, [_vp, _i32, _vp]),
             "adlbr_batch_config": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double),
@@ -329,3 +330,7 @@ def adlbr_batch_config(b):
 
 def adlbr_batch_destroy(b):
     _check(lib().adlbr_batch_destroy(b))
+
+
+def adlbr_unet_set_tensor_cores(net, on=True):
+    _check(lib().adlbr_unet_set_tensor_cores(net, 1 if on else 0))

@@ -228,6 +228,19 @@ adlbr_status unet_backward(adlbr_unet *n, const float *params, const float *gy, 
 adlbr_status unet_adam(float *params, const float *grads, float *m, float *v, int64_t n, double lr,
                        double b1, double b2, double eps, int t, cudaStream_t st);
 int64_t unet_num_params(const adlbr_unet *n);
+adlbr_status unet_set_tensor_cores(adlbr_unet *n, int on);
+// tensor-core 3x3 convolution + bias + ReLU (unet_tc.cu)
+size_t conv_tc_pack_elems(int Co, int Ci);
+struct ConvPackTable {   // the 3x3 layers packed by one conv_tc_pack launch
+    int n;
+    int co[10], ci[10];
+    int64_t w_off[10];   // weights in the flat parameter vector
+    int64_t out_off[10]; // packed BF16 elements, 8-element aligned
+};
+adlbr_status conv_tc_pack(const ConvPackTable &T, const float *params, __nv_bfloat16 *out, cudaStream_t st);
+bool conv_tc_supported(int Co, int Ci);
+adlbr_status conv_tc(int B, int Ci, int Co, int H, int W, const float *x, const __nv_bfloat16 *wpack,
+                     const float *bias, float *y, cudaStream_t st);
 void unet_shape(const adlbr_unet *n, int *cin, int *B, int *H, int *W);
 adlbr_status run_fcg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                      const adlbr_nn_precond *nn, int *iters_out, double *relres_out, cudaStream_t st);

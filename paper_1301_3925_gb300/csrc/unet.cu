@@ -36,6 +36,11 @@ struct adlbr_unet {
     float *g0, *g1, *gcat;  // gradient work buffers (largest activation size)
     float *wt;              // transposed / flipped weights for the data gradient
     int64_t n_params;
+    // inference on the tensor cores (unet_tc.cu): BF16 packed weights per layer
+    int tensor_cores;
+    int fwd_tc;             // the cached activations came from a tensor-core forward
+    __nv_bfloat16 *wpack;
+    size_t wpack_off[10];
 };
 
 namespace adlbr {
@@ -378,7 +383,22 @@ adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, 
     layer_table(n, L);
     const int H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int B = n->B;
+    if (n->tensor_cores) {
+        ConvPackTable T;
+        T.n = 10;
+        for (int l = 0; l < 10; ++l) {
+            T.co[l] = L[l].co;
+            T.ci[l] = L[l].ci;
+            T.w_off[l] = L[l].w_off;
+            T.out_off[l] = (int64_t)n->wpack_off[l];
+        }
+        if (adlbr_status e = conv_tc_pack(T, params, n->wpack, st)) return e;
+    }
+    n->fwd_tc = n->tensor_cores;
     auto cr = [&](int l, int h, int w, const float *x, float *y) {
+        if (n->tensor_cores)
+            return conv_tc(n->B, L[l].ci, L[l].co, h, w, x, n->wpack + n->wpack_off[l], params + L[l].b_off, y,
+                           st);
         return conv3x3(n, L[l].ci, L[l].co, h, w, x, params + L[l].w_off, params + L[l].b_off, y, true, st);
     };
     if (adlbr_status e = cr(0, H, W, xin, n->a1a)) return e;
@@ -536,9 +556,32 @@ adlbr_status unet_create(int cin, int c1, int c2, int c3, int B, int H, int W, a
     return ADLBR_OK;
 }
 
+// Forward convolutions on the tensor cores (BF16 operands, FP32 accumulation)
+// or back on the FP32 SIMT kernels.  The backward pass always uses FP32.
+adlbr_status unet_set_tensor_cores(adlbr_unet *n, int on) {
+    if (!n) return fail(ADLBR_E_ARG, "null network");
+    if (!on) {
+        n->tensor_cores = 0;
+        return ADLBR_OK;
+    }
+    Layer L[11];
+    layer_table(n, L);
+    size_t total = 0;
+    for (int l = 0; l < 10; ++l) {
+        if (!conv_tc_supported(L[l].co, L[l].ci))
+            return fail(ADLBR_E_SHAPE, "layer %d (%d -> %d channels) has no tensor-core form", l, L[l].ci, L[l].co);
+        n->wpack_off[l] = total;
+        total += (conv_tc_pack_elems(L[l].co, L[l].ci) + 63) / 64 * 64;
+    }
+    if (!n->wpack) ADLBR_CUDA(cudaMalloc(&n->wpack, total * sizeof(__nv_bfloat16)));
+    n->tensor_cores = 1;
+    return ADLBR_OK;
+}
+
 adlbr_status unet_destroy(adlbr_unet *n) {
     if (!n) return ADLBR_OK;
     if (n->mem) cudaFree(n->mem);
+    if (n->wpack) cudaFree(n->wpack);
     delete n;
     return ADLBR_OK;
 }
@@ -565,6 +608,8 @@ adlbr_status adlbr_unet_create(int cin, int c1, int c2, int c3, int batch, int H
 
 adlbr_status adlbr_unet_destroy(adlbr_unet *n) { return unet_destroy(n); }
 
+adlbr_status adlbr_unet_set_tensor_cores(adlbr_unet *n, int on) { return unet_set_tensor_cores(n, on); }
+
 int64_t adlbr_unet_num_params(const adlbr_unet *n) { return unet_num_params(n); }
 
 adlbr_status adlbr_unet_forward(adlbr_unet *n, const float *params, const float *x, float *y,
@@ -577,6 +622,7 @@ adlbr_status adlbr_unet_backward(adlbr_unet *n, const float *params, const float
                                  float *gparams, float *gx, cudaStream_t stream) {
     if (!n || !params || !gy || !gparams) return fail(ADLBR_E_ARG, "null argument");
     if (!n->x) return fail(ADLBR_E_ARG, "backward before any forward");
+    if (n->fwd_tc) return fail(ADLBR_E_ARG, "backward after a tensor-core (BF16) forward");
     return unet_backward(n, params, gy, gparams, gx, stream);
 }
 

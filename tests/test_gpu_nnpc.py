@@ -41,7 +41,7 @@ def test_precondition_matches_oracle():
     shape = (64, 96)
     h, oo, ow, diag, dt = _problem(shape, 5)
     theta = _params(1)
-    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0])
+    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0], tensor_cores=False)
     try:
         r = synth.u_uniform(shape, 6) - 0.5
         rd = dev(r.ravel(), t.float32)
@@ -79,12 +79,13 @@ def test_training_pairs_match_oracle_features():
     assert np.abs(tg - to).max() <= 1e-2 * np.abs(to).max() + 1e-6
 
 
-def test_fcg_converges_to_cg_solution():
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_fcg_converges_to_cg_solution(tensor_cores):
     t = torch()
     shape = (96, 112)
     h, oo, ow, diag, dt = _problem(shape, 3)
     theta = _params(2, scale_out=0.001)
-    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0])
+    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0], tensor_cores=tensor_cores)
     try:
         b = dev(synth.u_uniform(shape, 3).ravel(), t.float32)
         x1 = b.clone()

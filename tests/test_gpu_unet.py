@@ -67,3 +67,58 @@ def test_adam_step_matches_formula():
     th2 = a32[0] - lr * (m2 / (1 - b1 ** tt)) / (np.sqrt(v2 / (1 - b2 ** tt)) + eps)
     assert np.abs(d[0].double().cpu().numpy() - th2).max() <= 1e-6
     assert np.abs(d[2].double().cpu().numpy() - m2).max() <= 1e-6
+
+
+def _forward(net, th, xd, n_out):
+    t = torch()
+    y = t.empty(n_out, dtype=t.float32, device="cuda")
+    ab.adlbr_unet_forward(net, th, xd, y)
+    t.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+# widths that leave partial 128-pixel tiles at every level; channel mixes
+# with each of the 16 / 32 / 64-output kernels in the encoder and decoder
+@pytest.mark.parametrize("cin,c,B,H,W", [(25, (16, 32, 64), 1, 20, 200), (7, (64, 32, 16), 2, 12, 36),
+                                         (25, (16, 32, 64), 1, 256, 384)])
+def test_unet_tensor_core_forward_matches_fp32_and_oracle(cin, c, B, H, W):
+    t = torch()
+    kw = dict(c1=c[0], c2=c[1], c3=c[2])
+    g = np.random.default_rng(5)
+    theta = ou.init_params(cin, seed=2, **kw) + 0.05 * g.normal(size=ou.n_params(cin, **kw))
+    x = g.normal(size=(B, cin, H, W))
+    net = ab.adlbr_unet_create(cin, c[0], c[1], c[2], B, H, W)
+    try:
+        th = dev(theta, t.float32)
+        xd = dev(x.ravel(), t.float32)
+        y32 = _forward(net, th, xd, B * H * W).reshape(B, H, W)
+        ab.adlbr_unet_set_tensor_cores(net, True)
+        ytc = _forward(net, th, xd, B * H * W).reshape(B, H, W)
+        # a backward needs the FP32 activations
+        with pytest.raises(ab.AdlbrError):
+            ab.adlbr_unet_backward(net, th, t.zeros(B * H * W, dtype=t.float32, device="cuda"), t.empty_like(th))
+        ab.adlbr_unet_set_tensor_cores(net, False)
+        yback = _forward(net, th, xd, B * H * W).reshape(B, H, W)
+    finally:
+        ab.adlbr_unet_destroy(net)
+    assert np.isfinite(ytc).all()
+    assert np.array_equal(y32, yback)
+    scale = np.abs(y32).max()
+    # BF16 operands (8 significant bits) through 10 layers, FP32 accumulation
+    assert np.abs(ytc - y32).max() <= 3e-2 * scale
+    assert np.abs(ytc - y32).mean() <= 3e-3 * scale
+    if H * W <= 4096:
+        th32 = theta.astype(np.float32).astype(np.float64)
+        x32 = x.astype(np.float32).astype(np.float64)
+        for b in range(B):
+            yo, _ = ou.forward(th32, x32[b], **kw)
+            assert np.abs(ytc[b] - yo).max() <= 3e-2 * max(1e-30, np.abs(yo).max())
+
+
+def test_unet_tensor_cores_reject_unsupported_widths():
+    net = ab.adlbr_unet_create(3, 4, 6, 8, 1, 16, 16)
+    try:
+        with pytest.raises(ab.AdlbrError):
+            ab.adlbr_unet_set_tensor_cores(net, True)
+    finally:
+        ab.adlbr_unet_destroy(net)
