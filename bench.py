@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-3d", action="store_true", help="skip the 3D measurement and precision study")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-step measurement")
     p.add_argument("--no-ced3d", action="store_true", help="skip the 3D CED measurement")
+    p.add_argument("--no-spectral", action="store_true", help="skip the periodic spectral study")
     p.add_argument("--precision-steps", type=int, default=100)
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
@@ -324,6 +325,36 @@ def batch_measurement(peak, steps=20):
     finally:
         for h in hs:
             ab.adlbr_stencils_destroy(h)
+
+
+def spectral_measurement(n=256, k=7):
+    """The periodic spectral study (Fig. Eigen): the k smallest eigenvalues of
+    the scheme for D = [[19/2, 6], [6, 4]] on an n x n periodic grid by LOBPCG
+    on the FP64 operator (preconditioned by the library's CG), scaled by n^2
+    (h = 1/n) and set beside 4 pi^2 <m, D m>, the continuous eigenvalues."""
+    import time
+    import torch
+    from paper_1301_3925_gb300 import adlbr as ab
+    from paper_1301_3925_gb300 import spectral
+    D = np.array([[9.5, 6.0], [6.0, 4.0]])
+    planes = torch.tensor([D[0, 0], D[0, 1], D[1, 1]], dtype=torch.float64, device="cuda")
+    Dd = planes[:, None].expand(3, n * n).contiguous()
+    h = ab.adlbr_build_stencils(ab.grid((n, n), ab.PERIODIC), Dd, ab.F64, ab.F64)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        theta, _, its = spectral.lobpcg_smallest(h, n * n, k, tol=1e-10)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    r = np.arange(-8, 9)
+    mx, my = np.meshgrid(r, r, indexing="ij")
+    cont = np.sort(4 * np.pi ** 2 * (D[0, 0] * mx ** 2 + 2 * D[0, 1] * mx * my + D[1, 1] * my ** 2).ravel())[:k]
+    scaled = theta * n * n
+    return {"grid": [n, n], "D": D.tolist(), "k": k, "lobpcg_iters": its, "ms": ms,
+            "n2_lambda": [float(v) for v in scaled], "continuous": [float(v) for v in cont],
+            "max_rel_dev": float(np.abs(scaled - cont)[1:].max() / cont[1:].max())}
 
 
 def ced3d_measurement(steps=20):
@@ -664,6 +695,7 @@ def main():
     volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)
     batch = None if args.no_batch or rank != 0 else batch_measurement(peak)
     ced3d = None if args.no_ced3d or rank != 0 else ced3d_measurement()
+    spectral_study = None if args.no_spectral or rank != 0 else spectral_measurement()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -683,7 +715,7 @@ def main():
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
                 "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch,
-                "ced3d": ced3d}
+                "ced3d": ced3d, "spectral": spectral_study}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:
