@@ -327,7 +327,7 @@ def batch_measurement(peak, steps=20):
             ab.adlbr_stencils_destroy(h)
 
 
-def spectral_measurement(n=256, k=7):
+def spectral_measurement(n=128, k=7):
     """The periodic spectral study (Fig. Eigen): the k smallest eigenvalues of
     the scheme for D = [[19/2, 6], [6, 4]] on an n x n periodic grid by LOBPCG
     on the FP64 operator (preconditioned by the library's CG), scaled by n^2
