@@ -256,8 +256,10 @@ adlbr_status adlbr_unet_destroy(adlbr_unet *n);
  * forward of order 1e-2), weights repacked (one launch) at every forward
  * call.  For the inference path (the preconditioner): adlbr_unet_backward
  * returns ADLBR_E_ARG after a tensor-core forward.  on = 0 returns to the FP32
- * kernels.  ADLBR_E_SHAPE if a layer has other than 16,
- * 32 or 64 output channels or more than 160 input channels. */
+ * kernels.  ADLBR_E_SHAPE if a layer has other than 16, 32 or 64 output
+ * channels, or if its 9 packed weight taps and 4 staged input rows
+ * (2 * (9 Co + 4 * 136) * Kp bytes, Kp = Ci rounded up to 16) exceed 225 KB:
+ * at most 160 input channels for Co = 16, 128 for Co = 32, 96 for Co = 64. */
 adlbr_status adlbr_unet_set_tensor_cores(adlbr_unet *n, int on);
 /* Number of parameters (length of the flat parameter vector). */
 int64_t adlbr_unet_num_params(const adlbr_unet *n);
