@@ -86,29 +86,44 @@ __global__ void pack_weights_kernel(ConvPackTable T, const float *__restrict__ p
 }
 
 // Input row yy of image b into a slot: pixels x0 - 1 .. x0 + QR - 2, zero
-// outside the image and for the padding channels.
+// outside the image and for the padding channels.  Each thread takes SU
+// (pixel, 8-channel group) items at a time, with all their loads issued
+// before the first conversion (the copy is bound by load latency).
+constexpr int SU = 4;
 __device__ __forceinline__ void stage_row(unsigned char *slot, const float *__restrict__ xb, int Ci, int kp,
                                           int H, int W, int x0, int yy) {
-    const int G = kp / 8;
+    const int G = kp / 8, items = QR * G;
     const bool rin = (unsigned)yy < (unsigned)H;
     const int64_t plane = (int64_t)H * W;
-    for (int i = threadIdx.x; i < QR * G; i += 128) {
-        const int q = i % QR, g = i / QR;
-        const int gx = x0 - 1 + q;
-        float v[8];
+    const float *row = xb + (int64_t)yy * W;
+    for (int i0 = threadIdx.x; i0 < items; i0 += 128 * SU) {
+        float v[SU][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int ci = 8 * g + c;
-            v[c] = (rin && ci < Ci && (unsigned)gx < (unsigned)W) ? xb[ci * plane + (int64_t)yy * W + gx] : 0.f;
+        for (int u = 0; u < SU; ++u) {
+            const int i = i0 + u * 128;
+            const int q = i % QR, g = i / QR;
+            const int gx = x0 - 1 + q;
+            const bool in = i < items && rin && (unsigned)gx < (unsigned)W;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int ci = 8 * g + c;
+                v[u][c] = (in && ci < Ci) ? row[ci * plane + gx] : 0.f;
+            }
         }
-        uint4 pk;
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
-        pk.x = *reinterpret_cast<unsigned *>(&h0);
-        pk.y = *reinterpret_cast<unsigned *>(&h1);
-        pk.z = *reinterpret_cast<unsigned *>(&h2);
-        pk.w = *reinterpret_cast<unsigned *>(&h3);
-        *reinterpret_cast<uint4 *>(slot + (size_t)g * (QR * 16) + q * 16) = pk;
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int i = i0 + u * 128;
+            if (i >= items) break;
+            const int q = i % QR, g = i / QR;
+            uint4 pk;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]), h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4], v[u][5]), h3 = __floats2bfloat162_rn(v[u][6], v[u][7]);
+            pk.x = *reinterpret_cast<unsigned *>(&h0);
+            pk.y = *reinterpret_cast<unsigned *>(&h1);
+            pk.z = *reinterpret_cast<unsigned *>(&h2);
+            pk.w = *reinterpret_cast<unsigned *>(&h3);
+            *reinterpret_cast<uint4 *>(slot + (size_t)g * (QR * 16) + q * 16) = pk;
+        }
     }
 }
 
@@ -248,10 +263,10 @@ adlbr_status launch_tc(int B, int Ci, int H, int W, const float *x, const __nv_b
                                         (int)smem));
         set = smem;
     }
-    // strips of rows: about two CTAs per SM, at least 4 rows each
+    // strips of rows: about two CTAs per SM, at least 2 rows each
     const int cols = (W + TCM - 1) / TCM;
     const int64_t tiles = (int64_t)cols * H * B;
-    int rows = (int)std::max<int64_t>(4, (tiles + 2 * 152 - 1) / (2 * 152));
+    int rows = (int)std::max<int64_t>(2, (tiles + 2 * 152 - 1) / (2 * 152));
     rows = std::min(rows, H);
     dim3 grid(cols, (H + rows - 1) / rows, B);
     conv3x3_tc_kernel<CO><<<grid, 128, smem, st>>>(Ci, kp, H, W, rows, x, wpack, bias, y);
