@@ -628,16 +628,30 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     double best = INFINITY;
     int best_it = 0;
     bool fall_back = false;
+    auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
+        for (int k = 0; k < chunk; ++k) {
+            // q = (I + dt A) p is carried by the recurrences: no operator here
+            fcg_q_kernel<<<NB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
+            fcg_x_kernel<<<NB, RT, 0, cs>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
+            if (adlbr_status e = galerkin_direction<false>(s, W, nn->net, nn->params, dt, skip, cs)) return e;
+        }
+        ADLBR_CUDA(cudaGetLastError());
+        return ADLBR_OK;
+    };
+    // the chunk (about 25 launches per iteration, most of them the network's)
+    // is recorded once per solve and replayed; the first direction above ran
+    // uncaptured, so the kernels' one-time attribute settings are done
+    ChunkGraph graph;
+    if (!hook)
+        if (adlbr_status e = graph.capture(enqueue_chunk)) return e;
     while (it < maxit) {
         if (hook)
             if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
-        for (int k = 0; k < chunk; ++k) {
-            // q = (I + dt A) p is carried by the recurrences: no operator here
-            fcg_q_kernel<<<NB, RT, 0, st>>>(N, W.p, W.q, W.partials, W.S);
-            fcg_x_kernel<<<NB, RT, 0, st>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
-            if (adlbr_status e = galerkin_direction<false>(s, W, nn->net, nn->params, dt, skip, st)) return e;
+        if (graph.exec) {
+            ADLBR_CUDA(cudaGraphLaunch(graph.exec, st));
+        } else if (adlbr_status e = enqueue_chunk(st)) {
+            return e;
         }
-        ADLBR_CUDA(cudaGetLastError());
         it += chunk;
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
