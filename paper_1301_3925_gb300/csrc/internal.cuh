@@ -239,8 +239,15 @@ struct ConvPackTable {   // the 3x3 layers packed by one conv_tc_pack launch
 };
 adlbr_status conv_tc_pack(const ConvPackTable &T, const float *params, __nv_bfloat16 *out, cudaStream_t st);
 bool conv_tc_supported(int Co, int Ci);
-adlbr_status conv_tc(int B, int Ci, int Co, int H, int W, const float *x, const __nv_bfloat16 *wpack,
-                     const float *bias, float *y, cudaStream_t st);
+// y (BF16 [B][H][W][Co]) = ReLU(bias + conv3x3([x0 | x1])), x0 [B][H][W][C0],
+// x1 [B][H][W][C1] (C1 = 0: no second input), C0 + C1 = the packed Kp
+adlbr_status conv_tc(int B, int H, int W, const __nv_bfloat16 *x0, int C0, const __nv_bfloat16 *x1, int C1,
+                     int Co, const __nv_bfloat16 *wpack, const float *bias, __nv_bfloat16 *y, cudaStream_t st);
+adlbr_status tc_to_nhwc(int B, int C, int Cp, int64_t HW, const float *x, __nv_bfloat16 *y, cudaStream_t st);
+adlbr_status tc_pool(int B, int H2, int W2, int C, const __nv_bfloat16 *x, __nv_bfloat16 *y, cudaStream_t st);
+adlbr_status tc_up(int B, int H, int W, int C, const __nv_bfloat16 *x, __nv_bfloat16 *y, cudaStream_t st);
+adlbr_status tc_out1x1(int64_t n, int C, const __nv_bfloat16 *x, const float *w, const float *bias, float *y,
+                       cudaStream_t st);
 void unet_shape(const adlbr_unet *n, int *cin, int *B, int *H, int *W);
 adlbr_status run_fcg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                      const adlbr_nn_precond *nn, int *iters_out, double *relres_out, cudaStream_t st);

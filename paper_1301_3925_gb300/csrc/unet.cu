@@ -36,11 +36,14 @@ struct adlbr_unet {
     float *g0, *g1, *gcat;  // gradient work buffers (largest activation size)
     float *wt;              // transposed / flipped weights for the data gradient
     int64_t n_params;
-    // inference on the tensor cores (unet_tc.cu): BF16 packed weights per layer
+    // inference on the tensor cores (unet_tc.cu): BF16 packed weights per
+    // layer and BF16 channels-last activations (one allocation)
     int tensor_cores;
-    int fwd_tc;             // the cached activations came from a tensor-core forward
+    int fwd_tc;             // the last forward ran on the tensor cores
     __nv_bfloat16 *wpack;
     size_t wpack_off[10];
+    __nv_bfloat16 *hmem;
+    __nv_bfloat16 *hx, *h1a, *h1b, *hp1, *h2a, *h2b, *hp2, *h3a, *h3b, *hu3, *hd2a, *hd2b, *hu2, *hd1a, *hd1b;
 };
 
 namespace adlbr {
@@ -393,12 +396,37 @@ adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, 
             T.out_off[l] = (int64_t)n->wpack_off[l];
         }
         if (adlbr_status e = conv_tc_pack(T, params, n->wpack, st)) return e;
-    }
-    n->fwd_tc = n->tensor_cores;
-    auto cr = [&](int l, int h, int w, const float *x, float *y) {
-        if (n->tensor_cores)
-            return conv_tc(n->B, L[l].ci, L[l].co, h, w, x, n->wpack + n->wpack_off[l], params + L[l].b_off, y,
+        n->fwd_tc = 1;
+        const int c1 = n->c1, c2 = n->c2, c3 = n->c3, cp = (n->cin + 15) / 16 * 16;
+        auto cv = [&](int l, int h, int w, const __nv_bfloat16 *x0, int C0, const __nv_bfloat16 *x1, int C1,
+                      __nv_bfloat16 *y) {
+            return conv_tc(B, h, w, x0, C0, x1, C1, L[l].co, n->wpack + n->wpack_off[l], params + L[l].b_off, y,
                            st);
+        };
+        if (adlbr_status e = tc_to_nhwc(B, n->cin, cp, (int64_t)H * W, xin, n->hx, st)) return e;
+        if (adlbr_status e = cv(0, H, W, n->hx, cp, nullptr, 0, n->h1a)) return e;
+        if (adlbr_status e = cv(1, H, W, n->h1a, c1, nullptr, 0, n->h1b)) return e;
+        if (adlbr_status e = tc_pool(B, H2, W2, c1, n->h1b, n->hp1, st)) return e;
+        if (adlbr_status e = cv(2, H2, W2, n->hp1, c1, nullptr, 0, n->h2a)) return e;
+        if (adlbr_status e = cv(3, H2, W2, n->h2a, c2, nullptr, 0, n->h2b)) return e;
+        if (adlbr_status e = tc_pool(B, H4, W4, c2, n->h2b, n->hp2, st)) return e;
+        if (adlbr_status e = cv(4, H4, W4, n->hp2, c2, nullptr, 0, n->h3a)) return e;
+        if (adlbr_status e = cv(5, H4, W4, n->h3a, c3, nullptr, 0, n->h3b)) return e;
+        // [up(a3b), s2] and [up(d2b), s1]: the convolutions read both parts
+        if (adlbr_status e = tc_up(B, H4, W4, c3, n->h3b, n->hu3, st)) return e;
+        if (adlbr_status e = cv(6, H2, W2, n->hu3, c3, n->h2b, c2, n->hd2a)) return e;
+        if (adlbr_status e = cv(7, H2, W2, n->hd2a, c2, nullptr, 0, n->hd2b)) return e;
+        if (adlbr_status e = tc_up(B, H2, W2, c2, n->hd2b, n->hu2, st)) return e;
+        if (adlbr_status e = cv(8, H, W, n->hu2, c2, n->h1b, c1, n->hd1a)) return e;
+        if (adlbr_status e = cv(9, H, W, n->hd1a, c1, nullptr, 0, n->hd1b)) return e;
+        if (adlbr_status e = tc_out1x1((int64_t)B * H * W, c1, n->hd1b, params + L[10].w_off, params + L[10].b_off,
+                                       yout, st))
+            return e;
+        ADLBR_CUDA(cudaGetLastError());
+        return ADLBR_OK;
+    }
+    n->fwd_tc = 0;
+    auto cr = [&](int l, int h, int w, const float *x, float *y) {
         return conv3x3(n, L[l].ci, L[l].co, h, w, x, params + L[l].w_off, params + L[l].b_off, y, true, st);
     };
     if (adlbr_status e = cr(0, H, W, xin, n->a1a)) return e;
@@ -574,6 +602,24 @@ adlbr_status unet_set_tensor_cores(adlbr_unet *n, int on) {
         total += (conv_tc_pack_elems(L[l].co, L[l].ci) + 63) / 64 * 64;
     }
     if (!n->wpack) ADLBR_CUDA(cudaMalloc(&n->wpack, total * sizeof(__nv_bfloat16)));
+    if (!n->hmem) {
+        // BF16 channels-last activations of the tensor-core forward
+        const int64_t B = n->B, P1 = (int64_t)n->H * n->W, P2 = P1 / 4, P4 = P1 / 16;
+        const int64_t cp = (n->cin + 15) / 16 * 16;
+        const int64_t sizes[15] = {B * P1 * cp,     B * P1 * n->c1, B * P1 * n->c1, B * P2 * n->c1, B * P2 * n->c2,
+                                   B * P2 * n->c2,  B * P4 * n->c2, B * P4 * n->c3, B * P4 * n->c3, B * P2 * n->c3,
+                                   B * P2 * n->c2,  B * P2 * n->c2, B * P1 * n->c2, B * P1 * n->c1, B * P1 * n->c1};
+        int64_t tot = 0;
+        for (int64_t v : sizes) tot += (v + 63) / 64 * 64;
+        ADLBR_CUDA(cudaMalloc(&n->hmem, tot * sizeof(__nv_bfloat16)));
+        __nv_bfloat16 **dst[15] = {&n->hx,  &n->h1a, &n->h1b,  &n->hp1,  &n->h2a, &n->h2b,  &n->hp2, &n->h3a,
+                                   &n->h3b, &n->hu3, &n->hd2a, &n->hd2b, &n->hu2, &n->hd1a, &n->hd1b};
+        __nv_bfloat16 *q = n->hmem;
+        for (int k = 0; k < 15; ++k) {
+            *dst[k] = q;
+            q += (sizes[k] + 63) / 64 * 64;
+        }
+    }
     n->tensor_cores = 1;
     return ADLBR_OK;
 }
@@ -582,6 +628,7 @@ adlbr_status unet_destroy(adlbr_unet *n) {
     if (!n) return ADLBR_OK;
     if (n->mem) cudaFree(n->mem);
     if (n->wpack) cudaFree(n->wpack);
+    if (n->hmem) cudaFree(n->hmem);
     delete n;
     return ADLBR_OK;
 }

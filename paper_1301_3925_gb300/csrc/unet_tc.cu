@@ -1,43 +1,51 @@
-// 3x3 convolution + bias + ReLU on the 5th-generation tensor cores
-// (tcgen05), for the U-Net's inference path (the learned preconditioner).
+// The U-Net's inference path on the 5th-generation tensor cores (tcgen05),
+// for the learned preconditioner.  Activations are BF16, channels last
+// ([B][H][W][C], C a multiple of 8); every 3x3 convolution + bias + ReLU is
+// an implicit GEMM with an FP32 accumulator in tensor memory.
 //
-// Implicit GEMM without im2col.  A CTA (4 warps) owns 128 consecutive output
-// pixels of a strip of image rows, for all CO output channels:
+// Convolution.  A CTA (4 warps) owns 128 consecutive output pixels of a
+// strip of image rows, for all CO output channels:
 //   D[128 x CO] (TMEM, FP32) = sum over the 9 taps (dy, dx) and the channel
 //   blocks of 16 of A_(dy,dx)[128 x 16] * W_(dy,dx)[CO x 16]^T.
-// Input rows are staged once each, in BF16, as 130 pixels (x0 - 1 ..
-// x0 + 128) x Kp channels (Ci zero-padded to a multiple of 16) in the
-// no-swizzle K-major layout with the pixel as the row:
-//   element (q, ci) at (ci / 8) * LBO + q * 16 + (ci % 8) * 2, LBO = 136 * 16,
-// i.e. core matrices of 8 pixels x 8 channels, 8-row groups 128 B apart
-// (SBO = 128).  A shift of the tap by dx pixels is then a shift of the
-// descriptor's start address by 16 dx bytes: every tap of a staged row is
-// the same buffer.  The weights of all 9 taps stay in shared memory for the
-// whole strip, prepacked per tap in the K-major layout (co / 8) * 16 Kp +
-// (ci / 8) * 128 + (co % 8) * 16 + (ci % 8) * 2.
+// An input row is staged once: for every group of 8 channels one TMA copy of
+// a box of 130 pixels (x0 - 1 .. x0 + 128) x 8 channels lands as 130 rows of
+// 16 bytes, the no-swizzle K-major core-matrix layout with the pixel as the
+// matrix row (8-row groups 128 B apart: SBO = 128; channel groups LBO = 136 *
+// 16 B apart).  A tap shifted by dx pixels is the same buffer with the
+// descriptor's start address 16 dx bytes later, so there is no im2col.  TMA
+// fills pixels and rows outside the image with zeros (the padding of the
+// convolution).  The decoder's concatenated input [up, skip] is read from
+// its two tensors (the first groups from one map, the rest from the other),
+// so it is never materialised.  The weights of the 9 taps, prepacked per tap
+// in the K-major layout (co / 8) * 16 Kp + (ci / 8) * 128 + (co % 8) * 16 +
+// (ci % 8) * 2, stay in shared memory for the whole strip.
 //
-// Pipeline over the strip (4 input-row slots, 2 TMEM accumulators): while the
-// 9 Kp / 16 MMAs of output row y run (issued by one thread, committed to the
-// accumulator's mbarrier), the threads stage input row y + 2 and write output
-// row y - 1 from the other accumulator (tcgen05.ld, bias, ReLU, FP32 NCHW).
-// Waits are bounded; a CTA whose wait gives up writes NaN (the flexible
-// solver then falls back to plain CG) and stops issuing.
+// Pipeline over the strip: 5 input-row slots (4 where 5 do not fit), each
+// with its own mbarrier, filled two rows (one row) ahead by one thread; 2 TMEM
+// accumulators.  While the 9 Kp / 16 MMAs of output row y run (issued by one
+// thread, committed to the accumulator's mbarrier), the copies of the next
+// rows are in flight and the warps write output row y - 1 from the other
+// accumulator (tcgen05.ld, bias, ReLU, BF16, 16-byte stores).  Waits are bounded; a CTA whose wait gives up
+// writes NaN (the flexible solver then falls back to plain CG) and issues no
+// more MMAs.
 #include <algorithm>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "internal.cuh"
-
-struct adlbr_unet;
+#include "tma.cuh"
 
 namespace adlbr {
 
 namespace {
 
 constexpr int TCM = 128;          // output pixels per CTA (MMA M)
-constexpr int QR = TCM + 8;       // staged pixels per row slot (130 used), multiple of 8
-constexpr int NSLOT = 4;          // input-row ring
-constexpr unsigned kTcPolls = 1u << 22;
+constexpr int QB = TCM + 2;       // staged pixels per row (box width)
+constexpr int QR = TCM + 8;       // pixel rows per channel group in a slot (136 x 16 B)
+constexpr int NSLOT = 5;          // input-row ring: two rows of prefetch (4 slots, one row, where
+                                  // five do not fit)
 
 __device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -49,20 +57,6 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsig
 // byte offset of (co, ci) in one tap's packed weights (SBO = kp * 16, LBO = 128)
 __device__ __forceinline__ int cm_off(int row, int k, int kp) {
     return (row >> 3) * (kp * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
-}
-
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
-    for (unsigned k = 0; k < kTcPolls; ++k) {
-        unsigned done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(su32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 inline int kpad(int Ci) { return (Ci + 15) / 16 * 16; }
@@ -85,85 +79,69 @@ __global__ void pack_weights_kernel(ConvPackTable T, const float *__restrict__ p
     }
 }
 
-// Input row yy of image b into a slot: pixels x0 - 1 .. x0 + QR - 2, zero
-// outside the image and for the padding channels.  Each thread takes SU
-// (pixel, 8-channel group) items at a time, with all their loads issued
-// before the first conversion (the copy is bound by load latency).
-constexpr int SU = 4;
-__device__ __forceinline__ void stage_row(unsigned char *slot, const float *__restrict__ xb, int Ci, int kp,
-                                          int H, int W, int x0, int yy) {
-    const int G = kp / 8, items = QR * G;
-    const bool rin = (unsigned)yy < (unsigned)H;
-    const int64_t plane = (int64_t)H * W;
-    const float *row = xb + (int64_t)yy * W;
-    for (int i0 = threadIdx.x; i0 < items; i0 += 128 * SU) {
-        float v[SU][8];
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int i = i0 + u * 128;
-            const int q = i % QR, g = i / QR;
-            const int gx = x0 - 1 + q;
-            const bool in = i < items && rin && (unsigned)gx < (unsigned)W;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int ci = 8 * g + c;
-                v[u][c] = (in && ci < Ci) ? row[ci * plane + gx] : 0.f;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < SU; ++u) {
-            const int i = i0 + u * 128;
-            if (i >= items) break;
-            const int q = i % QR, g = i / QR;
-            uint4 pk;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[u][0], v[u][1]), h1 = __floats2bfloat162_rn(v[u][2], v[u][3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[u][4], v[u][5]), h3 = __floats2bfloat162_rn(v[u][6], v[u][7]);
-            pk.x = *reinterpret_cast<unsigned *>(&h0);
-            pk.y = *reinterpret_cast<unsigned *>(&h1);
-            pk.z = *reinterpret_cast<unsigned *>(&h2);
-            pk.w = *reinterpret_cast<unsigned *>(&h3);
-            *reinterpret_cast<uint4 *>(slot + (size_t)g * (QR * 16) + q * 16) = pk;
-        }
-    }
-}
+struct ConvMaps {
+    CUtensorMap m0, m1;   // [B][H][W][C0] and [B][H][W][C1] (m1 = m0 when there is one input)
+};
 
 template <int CO>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(int Ci, int kp, int H, int W, int rows_per_cta,
-                                                         const float *__restrict__ x,
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__ ConvMaps maps, int g0, int kp,
+                                                         int nslot, int H, int W, int rows_per_cta,
                                                          const __nv_bfloat16 *__restrict__ wpack,
-                                                         const float *__restrict__ bias, float *__restrict__ y) {
+                                                         const float *__restrict__ bias,
+                                                         __nv_bfloat16 *__restrict__ y) {
     static_assert(CO % 16 == 0 && CO >= 16 && CO <= 128, "MMA N");
     constexpr int TMEM_COLS = 2 * CO < 32 ? 32 : 2 * CO;   // two accumulators
     extern __shared__ __align__(1024) unsigned char sm[];
-    const size_t wbytes = (size_t)9 * CO * kp * 2, slot_bytes = (size_t)(kp / 8) * QR * 16;
-    unsigned char *sW = sm, *sX = sm + wbytes;   // weights, then NSLOT input-row slots
+    const int G = kp / 8;
+    const size_t wbytes = (size_t)9 * CO * kp * 2, slot_bytes = (size_t)G * QR * 16;
+    unsigned char *sW = sm, *sX = sm + wbytes;   // weights, then nslot input-row slots
+    const int ahead = nslot - 3;                 // rows of prefetch
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t sbar[NSLOT];
     const int t = threadIdx.x, warp = t >> 5;
     const int x0 = blockIdx.x * TCM, b = blockIdx.z;
     const int ya = blockIdx.y * rows_per_cta, yb = min(H, ya + rows_per_cta);
     if (ya >= yb) return;
-    const int64_t plane = (int64_t)H * W;
-    const float *xb = x + (int64_t)b * Ci * plane;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma::bar_init(&mbar[0], 1);
+        tma::bar_init(&mbar[1], 1);
+        for (int s = 0; s < nslot; ++s) tma::bar_init(&sbar[s], 1);
     }
-    // weights of the 9 taps (16-byte copies), input rows ya - 1 and ya
+    // input row yy (>= ya - 1) lives in slot (yy - ya + 1) % nslot; its fill is
+    // the ((yy - ya + 1) / nslot)-th of that slot
+    auto slot_of = [&](int yy) { return (yy - ya + 1) % nslot; };
+    auto parity_of = [&](int yy) { return (unsigned)(((yy - ya + 1) / nslot) & 1); };
+    auto issue_row = [&](int yy) {   // thread 0: the G copies of input row yy
+        const int s = slot_of(yy);
+        unsigned char *dst = sX + (size_t)s * slot_bytes;
+        tma::bar_expect_tx(&sbar[s], (unsigned)(G * QB * 16));
+        for (int g = 0; g < G; ++g) {
+            const bool first = g < g0;
+            const CUtensorMap *m = first ? &maps.m0 : &maps.m1;
+            const int c = 8 * (first ? g : g - g0);
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5}], [%6];" ::"r"(su32(dst + (size_t)g * QR * 16)),
+                "l"(reinterpret_cast<uint64_t>(m)), "r"(c), "r"(x0 - 1), "r"(yy), "r"(b), "r"(su32(&sbar[s]))
+                : "memory");
+        }
+    };
+    __syncthreads();   // barriers initialised
+    if (t == 0)
+        for (int yy = ya - 1; yy <= min(ya + ahead - 1, yb); ++yy) issue_row(yy);
+    // weights of the 9 taps (16-byte copies)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
         uint4 *dst = reinterpret_cast<uint4 *>(sW);
         for (int i = t; i < (int)(wbytes / 16); i += 128) dst[i] = src[i];
     }
-    auto slot = [&](int yy) { return sX + (size_t)(((yy % NSLOT) + NSLOT) % NSLOT) * slot_bytes; };
-    stage_row(slot(ya - 1), xb, Ci, kp, H, W, x0, ya - 1);
-    stage_row(slot(ya), xb, Ci, kp, H, W, x0, ya);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     // instruction descriptor: D f32, A and B bf16, both K-major, N = CO, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) |
                            ((uint32_t)(TCM >> 4) << 24);
@@ -171,46 +149,52 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(int Ci, int kp, int H, 
     bool ok = true;
     const int n = yb - ya;
     const int px = x0 + t;
+    const int64_t row_stride = (int64_t)W * CO;
     for (int j = 0; j <= n; ++j) {
         const int yo = ya + j;   // output row whose MMAs this iteration issues (j < n)
-        if (j < n) {
-            // input row yo + 1 goes to the slot of row yo - 3, last read by the
-            // MMAs of output row yo - 2 (waited for in the previous iteration)
-            stage_row(slot(yo + 1), xb, Ci, kp, H, W, x0, yo + 1);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        ok = __syncthreads_and(ok);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (j < n && t == 0 && ok) {
-            const uint32_t acc = tmem_base + (uint32_t)((j & 1) * CO);
-            bool first = true;
-            for (int dy = 0; dy < 3; ++dy) {
-                const unsigned abase = su32(slot(yo + dy - 1));
-                for (int dx = 0; dx < 3; ++dx) {
-                    const unsigned wbase = su32(sW) + (unsigned)((dy * 3 + dx) * CO * kp * 2);
-                    for (int s = 0; s < kp / 16; ++s) {
-                        const uint64_t da = smem_desc(abase + dx * 16 + s * 2 * lbo_a, lbo_a, 128);
-                        const uint64_t db = smem_desc(wbase + s * 256, 128, sbo_w);
-                        const unsigned accum = first ? 0u : 1u;
-                        first = false;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                            ::"r"(acc), "l"(da), "l"(db), "r"(idesc), "r"(accum)
-                            : "memory");
+            // row yo + ahead goes to the slot of row yo - 3, last read by the
+            // MMAs of output row yo - 2 (waited for in the previous iteration)
+            if (yo + ahead <= yb) issue_row(yo + ahead);
+            bool in = true;
+            for (int dy = 0; dy < 3 && in; ++dy)
+                in = tma::bar_wait(&sbar[slot_of(yo + dy - 1)], parity_of(yo + dy - 1));
+            ok = in;
+            if (ok) {
+                const uint32_t acc = tmem_base + (uint32_t)((j & 1) * CO);
+                bool first = true;
+                for (int dy = 0; dy < 3; ++dy) {
+                    const unsigned abase = su32(sX + (size_t)slot_of(yo + dy - 1) * slot_bytes);
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const unsigned wbase = su32(sW) + (unsigned)((dy * 3 + dx) * CO * kp * 2);
+                        for (int s = 0; s < kp / 16; ++s) {
+                            const uint64_t da = smem_desc(abase + dx * 16 + s * 2 * lbo_a, lbo_a, 128);
+                            const uint64_t db = smem_desc(wbase + s * 256, 128, sbo_w);
+                            const unsigned accum = first ? 0u : 1u;
+                            first = false;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                ::"r"(acc), "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                                : "memory");
+                        }
                     }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&mbar[j & 1]))
+                             : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(&bar[j & 1]))
-                         : "memory");
         }
         if (j >= 1) {   // epilogue of output row yo - 1
             const int jj = j - 1, yr = yo - 1;
-            ok = __syncthreads_and(ok && bar_wait(&bar[jj & 1], (jj >> 1) & 1));
+            ok = __syncthreads_and(ok) && tma::bar_wait(&mbar[jj & 1], (jj >> 1) & 1);
+            ok = __syncthreads_and(ok);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)((jj & 1) * CO);
+            __nv_bfloat16 *dst = y + ((int64_t)b * H + yr) * row_stride + (int64_t)px * CO;
 #pragma unroll
             for (int c = 0; c < CO; c += 16) {
                 uint32_t v[16];
@@ -222,40 +206,61 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(int Ci, int kp, int H, 
                       "=r"(v[14]), "=r"(v[15])
                     : "r"(taddr + c));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (px < W) {
+                uint32_t pk[8];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int co = c + q;
-                        float r = __uint_as_float(v[q]) + bias[co];
-                        r = ok ? fmaxf(r, 0.f) : __int_as_float(0x7fc00000);
-                        y[((int64_t)b * CO + co) * plane + (int64_t)yr * W + px] = r;
-                    }
+                for (int q = 0; q < 8; ++q) {
+                    float r0 = __uint_as_float(v[2 * q]) + bias[c + 2 * q];
+                    float r1 = __uint_as_float(v[2 * q + 1]) + bias[c + 2 * q + 1];
+                    r0 = ok ? fmaxf(r0, 0.f) : __int_as_float(0x7fc00000);
+                    r1 = ok ? fmaxf(r1, 0.f) : __int_as_float(0x7fc00000);
+                    __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+                    pk[q] = *reinterpret_cast<uint32_t *>(&h);
+                }
+                if (px < W) {
+                    uint4 *d4 = reinterpret_cast<uint4 *>(dst + c);
+                    d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
             }
         }
     }
+    // copies still in flight (the rows beyond a failed wait) are left to
+    // land: wait for every slot's last fill, bounded, before the exit
+    if (t == 0)
+        for (int yy = max(ya - 1, yb - nslot + 1); yy <= yb; ++yy) tma::bar_wait(&sbar[slot_of(yy)], parity_of(yy));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
 }
 
-// dynamic shared memory of one CTA
-size_t tc_smem(int Co, int Ci) {
-    const size_t kp = kpad(Ci);
-    return (size_t)9 * Co * kp * 2 + (size_t)NSLOT * (kp / 8) * QR * 16;
+// dynamic shared memory of one CTA with nslot row slots
+size_t tc_smem(int Co, int kp, int nslot) { return (size_t)9 * Co * kp * 2 + (size_t)nslot * (kp / 8) * QR * 16; }
+constexpr size_t kSmemCap = 225 * 1024;   // of 227 KB per CTA (about 1 KB static)
+
+// 4D map over a BF16 [B][H][W][C] tensor, box 8 channels x QB pixels x 1 x 1.
+bool encode_act(CUtensorMap *map, const __nv_bfloat16 *base, int B, int H, int W, int C) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tma::encoder();
+    if (!encode || ((uintptr_t)base & 15) || C % 8) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)QB, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int CO>
-adlbr_status launch_tc(int B, int Ci, int H, int W, const float *x, const __nv_bfloat16 *wpack, const float *bias,
-                       float *y, cudaStream_t st) {
-    const int kp = kpad(Ci);
+adlbr_status launch_tc(int B, int H, int W, const ConvMaps &maps, int g0, int kp, const __nv_bfloat16 *wpack,
+                       const float *bias, __nv_bfloat16 *y, cudaStream_t st) {
     // At most 512 / TMEM_COLS CTAs may hold TMEM on one SM at a time; a
     // floor on the shared memory keeps more from being resident (the SM has
     // 228 KB), so tcgen05.alloc never waits for another CTA.
     constexpr int TMEM_COLS = 2 * CO < 32 ? 32 : 2 * CO;
     constexpr int max_ctas = 512 / TMEM_COLS;
-    size_t smem = tc_smem(CO, Ci);
+    const int nslot = tc_smem(CO, kp, NSLOT) <= kSmemCap ? NSLOT : NSLOT - 1;
+    size_t smem = tc_smem(CO, kp, nslot);
     if (max_ctas < 16) smem = std::max(smem, (size_t)(228 * 1024 / (max_ctas + 1)));
     static size_t set = 0;
     if (smem > set) {
@@ -269,10 +274,106 @@ adlbr_status launch_tc(int B, int Ci, int H, int W, const float *x, const __nv_b
     int rows = (int)std::max<int64_t>(2, (tiles + 2 * 152 - 1) / (2 * 152));
     rows = std::min(rows, H);
     dim3 grid(cols, (H + rows - 1) / rows, B);
-    conv3x3_tc_kernel<CO><<<grid, 128, smem, st>>>(Ci, kp, H, W, rows, x, wpack, bias, y);
+    conv3x3_tc_kernel<CO><<<grid, 128, smem, st>>>(maps, g0, kp, nslot, H, W, rows, wpack, bias, y);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
+
+// ---- the layers around the convolutions (BF16, channels last) ------------
+
+// FP32 [B][C][HW] -> BF16 [B][HW][Cp], channels C .. Cp - 1 zero
+__global__ void to_nhwc_kernel(int B, int C, int Cp, int64_t HW, const float *__restrict__ x,
+                               __nv_bfloat16 *__restrict__ y) {
+    const int64_t n = (int64_t)B * HW * (Cp / 2);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c2 = (int)(i % (Cp / 2));
+        const int64_t p = i / (Cp / 2);
+        const int64_t b = p / HW, q = p % HW;
+        const int c = 2 * c2;
+        const float v0 = c < C ? x[(b * C + c) * HW + q] : 0.f;
+        const float v1 = c + 1 < C ? x[(b * C + c + 1) * HW + q] : 0.f;
+        reinterpret_cast<__nv_bfloat162 *>(y)[i] = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+__device__ __forceinline__ void unpack8(const uint4 &r, float (&f)[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 v = __bfloat1622float2(h[k]);
+        f[2 * k] = v.x;
+        f[2 * k + 1] = v.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 r;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    return r;
+}
+
+// 2 x 2 average pooling: [B][2H2][2W2][C] -> [B][H2][W2][C], 8 channels a thread
+__global__ void pool_nhwc_kernel(int B, int H2, int W2, int C, const __nv_bfloat16 *__restrict__ x,
+                                 __nv_bfloat16 *__restrict__ y) {
+    const int G = C / 8;
+    const int64_t n = (int64_t)B * H2 * W2 * G;
+    const uint4 *x4 = reinterpret_cast<const uint4 *>(x);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i % G);
+        int64_t p = i / G;
+        const int w = (int)(p % W2);
+        p /= W2;
+        const int h = (int)(p % H2);
+        const int64_t b = p / H2;
+        const int64_t r0 = ((b * 2 * H2 + 2 * h) * 2 * W2 + 2 * w) * G + g, r1 = r0 + (int64_t)2 * W2 * G;
+        float a[8], c[8], d[8], e[8], o[8];
+        unpack8(x4[r0], a);
+        unpack8(x4[r0 + G], c);
+        unpack8(x4[r1], d);
+        unpack8(x4[r1 + G], e);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = 0.25f * (a[k] + c[k] + d[k] + e[k]);
+        reinterpret_cast<uint4 *>(y)[i] = pack8(o);
+    }
+}
+
+// nearest 2x upsampling: [B][H][W][C] -> [B][2H][2W][C]
+__global__ void up_nhwc_kernel(int B, int H, int W, int C, const __nv_bfloat16 *__restrict__ x,
+                               __nv_bfloat16 *__restrict__ y) {
+    const int G = C / 8;
+    const int64_t n = (int64_t)B * 4 * H * W * G;
+    const uint4 *x4 = reinterpret_cast<const uint4 *>(x);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i % G);
+        int64_t p = i / G;
+        const int w2 = (int)(p % (2 * W));
+        p /= 2 * W;
+        const int h2 = (int)(p % (2 * H));
+        const int64_t b = p / (2 * H);
+        reinterpret_cast<uint4 *>(y)[i] = x4[((b * H + h2 / 2) * W + w2 / 2) * G + g];
+    }
+}
+
+// output layer: y[b][p] = bias + sum_c w[c] x[b][p][c] (FP32 out)
+__global__ void out1x1_nhwc_kernel(int64_t n, int C, const __nv_bfloat16 *__restrict__ x,
+                                   const float *__restrict__ w, const float *__restrict__ bias,
+                                   float *__restrict__ y) {
+    const int G = C / 8;
+    const uint4 *x4 = reinterpret_cast<const uint4 *>(x);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = bias[0];
+        for (int g = 0; g < G; ++g) {
+            float f[8];
+            unpack8(x4[i * G + g], f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = fmaf(w[8 * g + k], f[k], acc);
+        }
+        y[i] = acc;
+    }
+}
+
+unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
 }  // namespace
 
@@ -285,18 +386,50 @@ adlbr_status conv_tc_pack(const ConvPackTable &T, const float *params, __nv_bflo
 }
 
 bool conv_tc_supported(int Co, int Ci) {
-    // 227 KB of dynamic and static shared memory per CTA (1 KB static here)
-    return (Co == 16 || Co == 32 || Co == 64) && Ci >= 1 && tc_smem(Co, Ci) <= 225 * 1024;
+    return (Co == 16 || Co == 32 || Co == 64) && Ci >= 1 && tc_smem(Co, kpad(Ci), NSLOT - 1) <= kSmemCap;
 }
 
-adlbr_status conv_tc(int B, int Ci, int Co, int H, int W, const float *x, const __nv_bfloat16 *wpack,
-                     const float *bias, float *y, cudaStream_t st) {
+adlbr_status conv_tc(int B, int H, int W, const __nv_bfloat16 *x0, int C0, const __nv_bfloat16 *x1, int C1,
+                     int Co, const __nv_bfloat16 *wpack, const float *bias, __nv_bfloat16 *y, cudaStream_t st) {
+    const int kp = C0 + C1;
+    if (kp % 16 || C0 % 8 || C1 % 8 || (C1 && !x1) || W < 1 || H < 1)
+        return fail(ADLBR_E_ARG, "tensor-core convolution: %d + %d input channels", C0, C1);
+    ConvMaps maps;
+    if (!encode_act(&maps.m0, x0, B, H, W, C0) || (C1 && !encode_act(&maps.m1, x1, B, H, W, C1)))
+        return fail(ADLBR_E_CUDA, "tensor-core convolution: tensor map encoding failed");
+    if (!C1) maps.m1 = maps.m0;
+    const int g0 = C0 / 8;
     switch (Co) {
-    case 16: return launch_tc<16>(B, Ci, H, W, x, wpack, bias, y, st);
-    case 32: return launch_tc<32>(B, Ci, H, W, x, wpack, bias, y, st);
-    case 64: return launch_tc<64>(B, Ci, H, W, x, wpack, bias, y, st);
+    case 16: return launch_tc<16>(B, H, W, maps, g0, kp, wpack, bias, y, st);
+    case 32: return launch_tc<32>(B, H, W, maps, g0, kp, wpack, bias, y, st);
+    case 64: return launch_tc<64>(B, H, W, maps, g0, kp, wpack, bias, y, st);
     }
     return fail(ADLBR_E_ARG, "tensor-core convolution: %d output channels", Co);
+}
+
+adlbr_status tc_to_nhwc(int B, int C, int Cp, int64_t HW, const float *x, __nv_bfloat16 *y, cudaStream_t st) {
+    to_nhwc_kernel<<<grid_for((int64_t)B * HW * Cp / 2), 256, 0, st>>>(B, C, Cp, HW, x, y);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status tc_pool(int B, int H2, int W2, int C, const __nv_bfloat16 *x, __nv_bfloat16 *y, cudaStream_t st) {
+    pool_nhwc_kernel<<<grid_for((int64_t)B * H2 * W2 * C / 8), 256, 0, st>>>(B, H2, W2, C, x, y);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status tc_up(int B, int H, int W, int C, const __nv_bfloat16 *x, __nv_bfloat16 *y, cudaStream_t st) {
+    up_nhwc_kernel<<<grid_for((int64_t)B * 4 * H * W * C / 8), 256, 0, st>>>(B, H, W, C, x, y);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
+adlbr_status tc_out1x1(int64_t n, int C, const __nv_bfloat16 *x, const float *w, const float *bias, float *y,
+                       cudaStream_t st) {
+    out1x1_nhwc_kernel<<<grid_for(n), 256, 0, st>>>(n, C, x, w, bias, y);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
 }
 
 }  // namespace adlbr
