@@ -202,11 +202,8 @@ __global__ void __launch_bounds__(RT) fcg_init_kernel(int64_t N, const float *__
     }
     const double pr = block_sum_ff(s_rr);
     const double pb = block_sum_ff(s_bb);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = pb;
-    double tot;
-    if (finish_reduction(pr, partials, &S->count, tot)) {
-        double bb = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) bb += ((volatile double *)partials2)[k];
+    double tot, bb;
+    if (finish_reduction2(pr, pb, partials, partials2, &S->count, tot, bb)) {
         S->rr = tot;
         S->bb = bb;
         S->conv = (tot <= S->tol2 * bb) ? 1 : 0;
@@ -237,14 +234,9 @@ __global__ void __launch_bounds__(RT) fcg_z_kernel(int nx, int64_t N, const floa
     }
     const double prz = block_sum_ff(s_rz);
     const double poz = block_sum_ff(s_oz);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = poz;
-    double tot;
-    if (finish_reduction(prz, partials, &S->count, tot)) {
-        if (!FIRST) {
-            double oz = 0.0;
-            for (int k = 0; k < (int)gridDim.x; ++k) oz += ((volatile double *)partials2)[k];
-            S->beta = (tot - oz) / S->rz;
-        }
+    double tot, oz;
+    if (finish_reduction2(prz, poz, partials, partials2, &S->count, tot, oz)) {
+        if (!FIRST) S->beta = (tot - oz) / S->rz;
         S->rz = tot;
     }
 }
@@ -289,11 +281,8 @@ __global__ void __launch_bounds__(RT) fcg_gamma_kernel(int64_t N, const float *_
     }
     const double pn = block_sum_ff(sn);
     const double pm = block_sum_ff(sm);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = pm;
-    double tot;
-    if (finish_reduction(pn, partials, &S->count, tot)) {
-        double m = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) m += ((volatile double *)partials2)[k];
+    double tot, m;
+    if (finish_reduction2(pn, pm, partials, partials2, &S->count, tot, m)) {
         S->gamma = m > 0.0 ? tot / m : 0.0;
     }
 }
@@ -318,14 +307,9 @@ __global__ void __launch_bounds__(RT) fcg_z2_kernel(int64_t N, const float *__re
     }
     const double prz = block_sum_ff(s_rz);
     const double poz = block_sum_ff(s_oz);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = poz;
-    double tot;
-    if (finish_reduction(prz, partials, &S->count, tot)) {
-        if (!FIRST) {
-            double oz = 0.0;
-            for (int k = 0; k < (int)gridDim.x; ++k) oz += ((volatile double *)partials2)[k];
-            S->beta = (tot - oz) / S->rz;
-        }
+    double tot, oz;
+    if (finish_reduction2(prz, poz, partials, partials2, &S->count, tot, oz)) {
+        if (!FIRST) S->beta = (tot - oz) / S->rz;
         S->rz = tot;
     }
 }
@@ -418,11 +402,8 @@ __global__ void __launch_bounds__(RT) resid64_kernel(int64_t N, const float *__r
     }
     const double pr = block_sum(s_rr);
     const double pb = block_sum(s_bb);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = pb;
-    double tot;
-    if (finish_reduction(pr, partials, &S->count, tot)) {
-        double bb = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) bb += ((volatile double *)partials2)[k];
+    double tot, bb;
+    if (finish_reduction2(pr, pb, partials, partials2, &S->count, tot, bb)) {
         S->rr = tot;
         S->bb = bb;
     }

@@ -102,4 +102,35 @@ static __device__ __forceinline__ bool finish_reduction(double part, double *par
     return threadIdx.x == 0;
 }
 
+// The same for two sums at once; the last block reduces both arrays of
+// partials in parallel.
+static __device__ __forceinline__ bool finish_reduction2(double part, double part2, double *partials,
+                                                  double *partials2, unsigned int *count, double &total,
+                                                  double &total2) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = part;
+        partials2[blockIdx.x] = part2;
+        __threadfence();
+        unsigned int t = atomicAdd(count, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) {
+        s += ((volatile double *)partials)[b];
+        s2 += ((volatile double *)partials2)[b];
+    }
+    s = block_sum(s);
+    s2 = block_sum(s2);
+    if (threadIdx.x == 0) {
+        total = s;
+        total2 = s2;
+        *count = 0;
+    }
+    return threadIdx.x == 0;
+}
+
 }  // namespace adlbr
