@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--precision-steps", type=int, default=100)
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
+    p.add_argument("--profile-unet", action="store_true",
+                   help="only run four tensor-core U-Net forwards at 512^2 (for ncu launch lists)")
     return p.parse_args()
 
 
@@ -527,6 +529,31 @@ def config_dict():
 
 
 # ----------------------------------------------------------------- GPU arm
+def profile_unet():
+    """Four forwards of the 2048^2 preconditioner's network (25 -> 16/32/64
+    channels at 512^2, batch 1) on the tensor cores (profiling entry)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1301_3925_gb300 import adlbr as ab
+    from paper_1301_3925_gb300 import nn
+    H = W = 512
+    net = ab.adlbr_unet_create(nn.NF, 16, 32, 64, 1, H, W)
+    try:
+        P = ab.adlbr_unet_num_params(net)
+        th = torch.from_numpy(nn.init_params(P, nn.layer_shapes(nn.NF, 16, 32, 64), 1)).float().cuda()
+        x = torch.randn(nn.NF * H * W, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        y = torch.empty(H * W, device="cuda")
+        ab.adlbr_unet_set_tensor_cores(net, True)
+        for _ in range(4):
+            ab.adlbr_unet_forward(net, th, x, y)
+        torch.cuda.synchronize()
+    finally:
+        ab.adlbr_unet_destroy(net)
+    print(json.dumps({"profile_unet": {"y_abs_max": float(y.abs().max())}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -534,6 +561,8 @@ def main():
     import torch
     if args.profile_cg:
         return profile_cg()
+    if args.profile_unet:
+        return profile_unet()
 
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
