@@ -3,7 +3,7 @@
 // ([B][H][W][C], C a multiple of 8); every 3x3 convolution + bias + ReLU is
 // an implicit GEMM with an FP32 accumulator in tensor memory.
 //
-// Convolution.  A CTA (4 warps) owns 128 consecutive output pixels of a
+// Convolution.  A CTA (5 warps) owns 128 consecutive output pixels of a
 // strip of image rows, for all CO output channels:
 //   D[128 x CO] (TMEM, FP32) = sum over the 9 taps (dy, dx) and the channel
 //   blocks of 16 of A_(dy,dx)[128 x 16] * W_(dy,dx)[CO x 16]^T.
@@ -20,14 +20,15 @@
 // in the K-major layout (co / 8) * 16 Kp + (ci / 8) * 128 + (co % 8) * 16 +
 // (ci % 8) * 2, stay in shared memory for the whole strip.
 //
-// Pipeline over the strip: 5 input-row slots (4 where 5 do not fit), each
-// with its own mbarrier, filled two rows (one row) ahead by one thread; 2 TMEM
-// accumulators.  While the 9 Kp / 16 MMAs of output row y run (issued by one
-// thread, committed to the accumulator's mbarrier), the copies of the next
-// rows are in flight and the warps write output row y - 1 from the other
-// accumulator (tcgen05.ld, bias, ReLU, BF16, 16-byte stores).  Waits are bounded; a CTA whose wait gives up
-// writes NaN (the flexible solver then falls back to plain CG) and issues no
-// more MMAs.
+// Pipeline over the strip, warp-specialised: one lane of a producer warp
+// issues the TMA copies into 5 input-row slots (4 where 5 do not fit) and the
+// 9 Kp / 16 MMAs of each output row into one of 2 TMEM accumulators; four
+// epilogue warps read a finished accumulator (tcgen05.ld), add the bias,
+// apply the ReLU and write BF16 with 16-byte stores while the next row's MMAs
+// run.  The roles meet only at mbarriers (slot full / empty, accumulator full
+// / empty); every wait is bounded and gives up early once another role has
+// given up, and a CTA that gave up writes NaN (the flexible solver then falls
+// back to plain CG).
 #include <algorithm>
 
 #include <cuda.h>
@@ -83,23 +84,49 @@ struct ConvMaps {
     CUtensorMap m0, m1;   // [B][H][W][C0] and [B][H][W][C1] (m1 = m0 when there is one input)
 };
 
+__device__ __forceinline__ void bar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Bounded wait on a barrier phase that also gives up as soon as *abort is set.
+__device__ __forceinline__ bool bar_wait_or_abort(uint64_t *bar, unsigned parity, const volatile int *abort) {
+    for (unsigned k = 0; k < tma::kMaxPolls; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(su32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+// Warp-specialised: warps 0-3 are the epilogue (TMEM lanes 0-127), lane 0 of
+// warp 4 is the producer (TMA copies and MMAs).  Barriers: full[s] (copies
+// of slot s landed), empty[s] (the MMAs of the last output row reading slot
+// s are done; committed by the producer), afull[b] (accumulator b holds a
+// finished row), aempty[b] (the 4 epilogue warps have read accumulator b).
+constexpr int NT_TC = 160;
+
 template <int CO>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__ ConvMaps maps, int g0, int kp,
-                                                         int nslot, int H, int W, int rows_per_cta,
-                                                         const __nv_bfloat16 *__restrict__ wpack,
-                                                         const float *__restrict__ bias,
-                                                         __nv_bfloat16 *__restrict__ y) {
+__global__ void __launch_bounds__(NT_TC) conv3x3_tc_kernel(const __grid_constant__ ConvMaps maps, int g0, int kp,
+                                                           int nslot, int H, int W, int rows_per_cta,
+                                                           const __nv_bfloat16 *__restrict__ wpack,
+                                                           const float *__restrict__ bias,
+                                                           __nv_bfloat16 *__restrict__ y) {
     static_assert(CO % 16 == 0 && CO >= 16 && CO <= 128, "MMA N");
     constexpr int TMEM_COLS = 2 * CO < 32 ? 32 : 2 * CO;   // two accumulators
     extern __shared__ __align__(1024) unsigned char sm[];
     const int G = kp / 8;
     const size_t wbytes = (size_t)9 * CO * kp * 2, slot_bytes = (size_t)G * QR * 16;
     unsigned char *sW = sm, *sX = sm + wbytes;   // weights, then nslot input-row slots
-    const int ahead = nslot - 3;                 // rows of prefetch
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ __align__(8) uint64_t sbar[NSLOT];
-    const int t = threadIdx.x, warp = t >> 5;
+    __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT], afull[2], aempty[2];
+    __shared__ volatile int abort_flag;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int x0 = blockIdx.x * TCM, b = blockIdx.z;
     const int ya = blockIdx.y * rows_per_cta, yb = min(H, ya + rows_per_cta);
     if (ya >= yb) return;
@@ -109,70 +136,76 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (t == 0) {
-        tma::bar_init(&mbar[0], 1);
-        tma::bar_init(&mbar[1], 1);
-        for (int s = 0; s < nslot; ++s) tma::bar_init(&sbar[s], 1);
-    }
-    // input row yy (>= ya - 1) lives in slot (yy - ya + 1) % nslot; its fill is
-    // the ((yy - ya + 1) / nslot)-th of that slot
-    auto slot_of = [&](int yy) { return (yy - ya + 1) % nslot; };
-    auto parity_of = [&](int yy) { return (unsigned)(((yy - ya + 1) / nslot) & 1); };
-    auto issue_row = [&](int yy) {   // thread 0: the G copies of input row yy
-        const int s = slot_of(yy);
-        unsigned char *dst = sX + (size_t)s * slot_bytes;
-        tma::bar_expect_tx(&sbar[s], (unsigned)(G * QB * 16));
-        for (int g = 0; g < G; ++g) {
-            const bool first = g < g0;
-            const CUtensorMap *m = first ? &maps.m0 : &maps.m1;
-            const int c = 8 * (first ? g : g - g0);
-            asm volatile(
-                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4, %5}], [%6];" ::"r"(su32(dst + (size_t)g * QR * 16)),
-                "l"(reinterpret_cast<uint64_t>(m)), "r"(c), "r"(x0 - 1), "r"(yy), "r"(b), "r"(su32(&sbar[s]))
-                : "memory");
+        for (int s = 0; s < nslot; ++s) {
+            tma::bar_init(&full[s], 1);
+            tma::bar_init(&empty[s], 1);
         }
-    };
-    __syncthreads();   // barriers initialised
-    if (t == 0)
-        for (int yy = ya - 1; yy <= min(ya + ahead - 1, yb); ++yy) issue_row(yy);
-    // weights of the 9 taps (16-byte copies)
-    {
+        for (int k = 0; k < 2; ++k) {
+            tma::bar_init(&afull[k], 1);
+            tma::bar_init(&aempty[k], 4);
+        }
+        abort_flag = 0;
+    }
+    {   // weights of the 9 taps (16-byte copies)
         const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
         uint4 *dst = reinterpret_cast<uint4 *>(sW);
-        for (int i = t; i < (int)(wbytes / 16); i += 128) dst[i] = src[i];
+        for (int i = t; i < (int)(wbytes / 16); i += NT_TC) dst[i] = src[i];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    // instruction descriptor: D f32, A and B bf16, both K-major, N = CO, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) |
-                           ((uint32_t)(TCM >> 4) << 24);
-    const unsigned lbo_a = QR * 16, sbo_w = (unsigned)kp * 16;
-    bool ok = true;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int n = yb - ya;
-    const int px = x0 + t;
-    const int64_t row_stride = (int64_t)W * CO;
-    for (int j = 0; j <= n; ++j) {
-        const int yo = ya + j;   // output row whose MMAs this iteration issues (j < n)
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(ok);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (j < n && t == 0 && ok) {
-            // row yo + ahead goes to the slot of row yo - 3, last read by the
-            // MMAs of output row yo - 2 (waited for in the previous iteration)
-            if (yo + ahead <= yb) issue_row(yo + ahead);
-            bool in = true;
-            for (int dy = 0; dy < 3 && in; ++dy)
-                in = tma::bar_wait(&sbar[slot_of(yo + dy - 1)], parity_of(yo + dy - 1));
-            ok = in;
-            if (ok) {
+    // input row yy (>= ya - 1) lives in slot (yy - ya + 1) % nslot; it is
+    // that slot's fill number (yy - ya + 1) / nslot
+    auto slot_of = [&](int yy) { return (yy - ya + 1) % nslot; };
+    auto fill_of = [&](int yy) { return (yy - ya + 1) / nslot; };
+    if (warp == 4) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) |
+                                   ((uint32_t)(TCM >> 4) << 24);
+            const unsigned lbo_a = QR * 16, sbo_w = (unsigned)kp * 16;
+            bool ok = true;
+            // the copies of input row r into its slot, once the slot's previous
+            // row is no longer read (its freeing commit is done)
+            auto load = [&](int r) -> bool {
+                const int s = slot_of(r), k = fill_of(r);
+                if (k >= 1 && !bar_wait_or_abort(&empty[s], (unsigned)((k - 1) & 1), &abort_flag)) return false;
+                unsigned char *dst = sX + (size_t)s * slot_bytes;
+                tma::bar_expect_tx(&full[s], (unsigned)(G * QB * 16));
+                for (int g = 0; g < G; ++g) {
+                    const bool first = g < g0;
+                    const CUtensorMap *m = first ? &maps.m0 : &maps.m1;
+                    const int c = 8 * (first ? g : g - g0);
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3, %4, %5}], [%6];" ::"r"(su32(dst + (size_t)g * QR * 16)),
+                        "l"(reinterpret_cast<uint64_t>(m)), "r"(c), "r"(x0 - 1), "r"(r), "r"(b),
+                        "r"(su32(&full[s]))
+                        : "memory");
+                }
+                return true;
+            };
+            int next = ya - 1;   // next input row to copy
+            for (; ok && next <= min(yb, ya - 1 + nslot - 1); ++next) ok = load(next);
+            int issued = 0;
+            for (int j = 0; ok && j < n; ++j) {
+                const int yo = ya + j;
+                for (int dy = 0; ok && dy < 3; ++dy)
+                    ok = bar_wait_or_abort(&full[slot_of(yo + dy - 1)], (unsigned)(fill_of(yo + dy - 1) & 1),
+                                           &abort_flag);
+                if (ok && j >= 2) ok = bar_wait_or_abort(&aempty[j & 1], (unsigned)(((j >> 1) - 1) & 1), &abort_flag);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc = tmem_base + (uint32_t)((j & 1) * CO);
                 bool first = true;
                 for (int dy = 0; dy < 3; ++dy) {
                     const unsigned abase = su32(sX + (size_t)slot_of(yo + dy - 1) * slot_bytes);
                     for (int dx = 0; dx < 3; ++dx) {
-                        const unsigned wbase = su32(sW) + (unsigned)((dy * 3 + dx) * CO * kp * 2);
+                        const unsigned wb = su32(sW) + (unsigned)((dy * 3 + dx) * CO * kp * 2);
                         for (int s = 0; s < kp / 16; ++s) {
                             const uint64_t da = smem_desc(abase + dx * 16 + s * 2 * lbo_a, lbo_a, 128);
-                            const uint64_t db = smem_desc(wbase + s * 256, 128, sbo_w);
+                            const uint64_t db = smem_desc(wb + s * 256, 128, sbo_w);
                             const unsigned accum = first ? 0u : 1u;
                             first = false;
                             asm volatile(
@@ -184,17 +217,33 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 su32(&mbar[j & 1]))
+                                 su32(&afull[j & 1]))
                              : "memory");
+                // input row yo - 1 is read by no later output row
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&empty[slot_of(yo - 1)]))
+                             : "memory");
+                issued = j + 1;
+                // refill slots freed by output rows up to yo - 1
+                for (; ok && next <= min(yb, yo + nslot - 2); ++next) ok = load(next);
             }
+            if (!ok) abort_flag = 1;
+            // nothing may be in flight when the CTA exits: the last MMAs, and
+            // the copies of the last nslot rows (bounded waits)
+            if (issued > 0) tma::bar_wait(&afull[(issued - 1) & 1], (unsigned)(((issued - 1) >> 1) & 1));
+            for (int r = max(ya - 1, next - nslot); r < next; ++r)
+                tma::bar_wait(&full[slot_of(r)], (unsigned)(fill_of(r) & 1));
         }
-        if (j >= 1) {   // epilogue of output row yo - 1
-            const int jj = j - 1, yr = yo - 1;
-            ok = __syncthreads_and(ok) && tma::bar_wait(&mbar[jj & 1], (jj >> 1) & 1);
-            ok = __syncthreads_and(ok);
+        __syncwarp();   // the warp meets again before the block barrier below
+    } else {
+        const int px = x0 + t;   // this thread's pixel = TMEM lane
+        const int64_t row_stride = (int64_t)W * CO;
+        for (int j = 0; j < n; ++j) {
+            const bool ok = bar_wait_or_abort(&afull[j & 1], (unsigned)((j >> 1) & 1), &abort_flag);
+            if (!ok) abort_flag = 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)((jj & 1) * CO);
-            __nv_bfloat16 *dst = y + ((int64_t)b * H + yr) * row_stride + (int64_t)px * CO;
+            const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)((j & 1) * CO);
+            uint32_t pk[CO / 2];
 #pragma unroll
             for (int c = 0; c < CO; c += 16) {
                 uint32_t v[16];
@@ -206,7 +255,6 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                       "=r"(v[14]), "=r"(v[15])
                     : "r"(taddr + c));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                uint32_t pk[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     float r0 = __uint_as_float(v[2 * q]) + bias[c + 2 * q];
@@ -214,22 +262,23 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                     r0 = ok ? fmaxf(r0, 0.f) : __int_as_float(0x7fc00000);
                     r1 = ok ? fmaxf(r1, 0.f) : __int_as_float(0x7fc00000);
                     __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
-                    pk[q] = *reinterpret_cast<uint32_t *>(&h);
+                    pk[c / 2 + q] = *reinterpret_cast<uint32_t *>(&h);
                 }
-                if (px < W) {
-                    uint4 *d4 = reinterpret_cast<uint4 *>(dst + c);
-                    d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
+            }
+            // the accumulator is read: hand it back to the producer
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&aempty[j & 1]);
+            if (px < W) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(y + ((int64_t)b * H + ya + j) * row_stride + (int64_t)px * CO);
+#pragma unroll
+                for (int q = 0; q < CO / 8; ++q) d4[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
             }
         }
     }
-    // copies still in flight (the rows beyond a failed wait) are left to
-    // land: wait for every slot's last fill, bounded, before the exit
-    if (t == 0)
-        for (int yy = max(ya - 1, yb - nslot + 1); yy <= yb; ++yy) tma::bar_wait(&sbar[slot_of(yy)], parity_of(yy));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
 }
@@ -274,7 +323,7 @@ adlbr_status launch_tc(int B, int H, int W, const ConvMaps &maps, int g0, int kp
     int rows = (int)std::max<int64_t>(2, (tiles + 2 * 152 - 1) / (2 * 152));
     rows = std::min(rows, H);
     dim3 grid(cols, (H + rows - 1) / rows, B);
-    conv3x3_tc_kernel<CO><<<grid, 128, smem, st>>>(maps, g0, kp, nslot, H, W, rows, wpack, bias, y);
+    conv3x3_tc_kernel<CO><<<grid, NT_TC, smem, st>>>(maps, g0, kp, nslot, H, W, rows, wpack, bias, y);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
