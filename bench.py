@@ -184,6 +184,55 @@ def time_ms(fn, reps, stream):
 
 
 # ----------------------------------------------------------------- sub-measurements
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def unet_forward_measurement(params, H, W, reps=20):
+    """The preconditioner's network (25 -> 16/32/64 channels, batch 1, H x W)
+    on the tensor cores and on the FP32 SIMT kernels: CUDA-event times over
+    `reps` forwards, and the tensor-core forward's dense FLOPs (2 per
+    multiply-add of every convolution) against the measured BF16 peak."""
+    import torch
+    from paper_1301_3925_gb300 import adlbr as ab
+    from paper_1301_3925_gb300 import nn
+    net = ab.adlbr_unet_create(nn.NF, 16, 32, 64, 1, H, W)
+    try:
+        x = torch.randn(nn.NF * H * W, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        y = torch.empty(H * W, device="cuda")
+        res = {}
+        for name, tc in (("fp32_ms", False), ("tc_ms", True)):
+            ab.adlbr_unet_set_tensor_cores(net, tc)
+            for _ in range(3):
+                ab.adlbr_unet_forward(net, params, x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                ab.adlbr_unet_forward(net, params, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / reps
+    finally:
+        ab.adlbr_unet_destroy(net)
+    # per layer: (co, ci, k) at full, half, quarter resolution
+    scale = [1, 1, 4, 4, 16, 16, 4, 4, 1, 1, 1]
+    flops = sum(2.0 * co * ci * k * k * H * W / sc
+                for (co, ci, k), sc in zip(nn.layer_shapes(nn.NF, 16, 32, 64), scale))
+    pk, src = bf16_peak()
+    tf = flops / (res["tc_ms"] * 1e-3) / 1e12
+    res.update({"grid": [H, W], "gflop": flops / 1e9, "tc_tflops": tf, "bf16_peak_tflops": pk,
+                "peak_source": src, "frac_bf16_peak": tf / pk,
+                "note": "latency-bound: per-row copy / MMA / epilogue chains over short strips"})
+    return res
+
+
 def implicit_measurement(peak):
     """Implicit step (I + dt A) x = u_n on 2048^2, smooth random orientation,
     kappa in [1, 50], dt = 200 / max A_zz, tolerance 1e-6: plain CG, flexible
@@ -237,6 +286,7 @@ def implicit_measurement(peak):
             out[name] = {"iters": r[-1][0], "relres": r[-1][1], "ms": float(np.median([c[2] for c in r])),
                          "fell_back_to_cg": bool(r[-1][3])}
         out["nn_vs_cg_wallclock"] = out["cg"]["ms"] / out["nn_fcg"]["ms"]
+        out["unet_forward"] = unet_forward_measurement(params, n // nn.RF, n // nn.RF)
         return out
     finally:
         ab.adlbr_stencils_destroy(h)
