@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(NT_TC) conv3x3_tc_kernel(const __grid_constant
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t full[NSLOT], empty[NSLOT], afull[2], aempty[2];
     __shared__ volatile int abort_flag;
+    __shared__ float sbias[CO];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int x0 = blockIdx.x * TCM, b = blockIdx.z;
     const int ya = blockIdx.y * rows_per_cta, yb = min(H, ya + rows_per_cta);
@@ -146,10 +147,11 @@ __global__ void __launch_bounds__(NT_TC) conv3x3_tc_kernel(const __grid_constant
         }
         abort_flag = 0;
     }
-    {   // weights of the 9 taps (16-byte copies)
+    {   // weights of the 9 taps (16-byte copies) and the bias
         const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
         uint4 *dst = reinterpret_cast<uint4 *>(sW);
         for (int i = t; i < (int)(wbytes / 16); i += NT_TC) dst[i] = src[i];
+        if (t < CO) sbias[t] = bias[t];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -257,8 +259,8 @@ __global__ void __launch_bounds__(NT_TC) conv3x3_tc_kernel(const __grid_constant
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    float r0 = __uint_as_float(v[2 * q]) + bias[c + 2 * q];
-                    float r1 = __uint_as_float(v[2 * q + 1]) + bias[c + 2 * q + 1];
+                    float r0 = __uint_as_float(v[2 * q]) + sbias[c + 2 * q];
+                    float r1 = __uint_as_float(v[2 * q + 1]) + sbias[c + 2 * q + 1];
                     r0 = ok ? fmaxf(r0, 0.f) : __int_as_float(0x7fc00000);
                     r1 = ok ? fmaxf(r1, 0.f) : __int_as_float(0x7fc00000);
                     __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);

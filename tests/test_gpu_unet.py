@@ -99,6 +99,11 @@ def test_unet_tensor_core_forward_matches_fp32_and_oracle(cin, c, B, H, W):
             ab.adlbr_unet_backward(net, th, t.zeros(B * H * W, dtype=t.float32, device="cuda"), t.empty_like(th))
         ab.adlbr_unet_set_tensor_cores(net, False)
         yback = _forward(net, th, xd, B * H * W).reshape(B, H, W)
+        # after an FP32 forward the backward runs again
+        gth = t.empty_like(th)
+        ab.adlbr_unet_backward(net, th, t.ones(B * H * W, dtype=t.float32, device="cuda"), gth)
+        t.cuda.synchronize()
+        assert t.isfinite(gth).all()
     finally:
         ab.adlbr_unet_destroy(net)
     assert np.isfinite(ytc).all()
