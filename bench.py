@@ -41,9 +41,9 @@ ALU_OPS_PER_POINT = 2 * 7 + 7 + 2 * 3 * 25 + 20
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch at 4096^2, from ncu captures of the
 # current kernels (the summaries under profiles/ give the commands)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.168e6 + 140.913e6, "build2d_kernel": 201.526e6 + 229.140e6,
+TRAFFIC_4096 = {"ced_fused_kernel": 67.180e6 + 140.324e6, "build2d_kernel": 201.348e6 + 229.138e6,
                 # operator + finalize
-                "explicit_step": 402.731e6 + 51.889e6 + 134.224e6 + 22.103e6}
+                "explicit_step": 402.735e6 + 51.184e6 + 134.225e6 + 21.878e6}
 
 
 def parse():
