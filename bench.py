@@ -39,8 +39,9 @@ SEED = 1
 # 2 x 3 x 25, eigen epilogue 20; and the FP32 issue peak it is held against.
 ALU_OPS_PER_POINT = 2 * 7 + 7 + 2 * 3 * 25 + 20
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one launch at 4096^2, from ncu captures of the
-# current kernels (the summaries under profiles/ give the commands)
+# DRAM bytes (read + write) of one launch at 4096^2, from an ncu capture of the
+# current kernels (dram__bytes_read.sum + dram__bytes_write.sum, one launch each,
+# second warm-up step of this benchmark's CED step)
 TRAFFIC_4096 = {"ced_fused_kernel": 67.180e6 + 140.324e6, "build2d_kernel": 201.348e6 + 229.138e6,
                 # operator + finalize
                 "explicit_step": 402.735e6 + 51.184e6 + 134.225e6 + 21.878e6}
