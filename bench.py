@@ -268,6 +268,9 @@ def implicit_measurement(peak):
         solve()
         cg = [solve() for _ in range(3)]
         out["cg"] = {"iters": cg[-1][0], "relres": cg[-1][1], "ms": float(np.median([c[2] for c in cg]))}
+        solve(2)
+        jp = [solve(2) for _ in range(3)]
+        out["jacobi_pcg"] = {"iters": jp[-1][0], "relres": jp[-1][1], "ms": float(np.median([c[2] for c in jp]))}
         t0 = time.perf_counter()
         rhs = [torch.from_numpy(synth.u_uniform((n, n), 100 + k).astype(np.float32).ravel()).cuda()
                for k in range(3)]
@@ -287,6 +290,7 @@ def implicit_measurement(peak):
             out[name] = {"iters": r[-1][0], "relres": r[-1][1], "ms": float(np.median([c[2] for c in r])),
                          "fell_back_to_cg": bool(r[-1][3])}
         out["nn_vs_cg_wallclock"] = out["cg"]["ms"] / out["nn_fcg"]["ms"]
+        out["jacobi_pcg_vs_cg_wallclock"] = out["cg"]["ms"] / out["jacobi_pcg"]["ms"]
         out["unet_forward"] = unet_forward_measurement(params, n // nn.RF, n // nn.RF)
         return out
     finally:

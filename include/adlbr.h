@@ -212,7 +212,10 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  *              tenfold above its best value or does not halve within 100
  *              iterations, the solve restarts from the initial guess with
  *              plain CG (iters_out then counts both; adlbr_last_fallback()
- *              returns 1).
+ *              returns 1).  2: CG preconditioned by the diagonal
+ *              d = 1 + dt A_zz (z = r / d; alpha = <r,z> / <p,(I + dt A) p>,
+ *              beta = <r,z>_new / <r,z>_old), the same stopping test and
+ *              refinement rounds as plain CG; 2D and 3D.
  *  nn          preconditioner parameters (precond == 1), else ignored.
  *  iters_out   iterations performed (may be NULL).
  *  relres_out  final true relative residual |rhs - (I + dt A) x| / |rhs|.

@@ -186,6 +186,8 @@ adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, do
     if (precond == 1)
         return run_fcg(s, (const float *)rhs, (float *)x, dt, rtol, maxit,
                        (const adlbr_nn_precond *)nn, iters_out, relres_out, stream);
+    if (precond == 2)
+        return run_pcg_jacobi(s, (const float *)rhs, (float *)x, dt, rtol, maxit, iters_out, relres_out, stream);
     if (precond != 0) return fail(ADLBR_E_ARG, "unknown preconditioner %d", precond);
     return run_cg(s, (const float *)rhs, (float *)x, dt, rtol, maxit, iters_out, relres_out, stream);
 }

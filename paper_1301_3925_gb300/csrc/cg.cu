@@ -15,6 +15,9 @@
 //   K2  <p, q> ; last block: alpha = rr / <p,q>
 //   K3  x += alpha p ; r -= alpha q ; <r, r> ; last block: beta, flag
 //   K4  p <- r + beta p ; q <- p
+// JAC (CG preconditioned by the diagonal d = 1 + dt A_zz, z = r / d, held as
+// 1 / d): alpha = <r,z> / <p,q>, K3 also sums <r,z>, beta = <r,z>_new /
+// <r,z>_old, K4 sets p <- z + beta p.  The stopping test stays |r| <= rtol |b|.
 // (no kernel stores a constant over a value it has just loaded: such a
 // store waits for the load and a vector pass with one runs at a fraction of
 // the HBM rate on this GPU)
@@ -31,7 +34,7 @@ namespace {
 constexpr int RB = 1216;  // blocks of the vector kernels (8 per SM on 152 SMs)
 
 struct CgState {
-    double rr, rr_new, pq, alpha, beta, bb, tol2;
+    double rr, rr_new, pq, alpha, beta, bb, tol2, rz;
     int conv, iters, max_iters;  // conv: 0 running, 1 converged, 2 iteration limit, 3 non-finite
     unsigned int count;          // last-block ticket
 };
@@ -40,42 +43,64 @@ struct CgState {
 // (acc holds dt A x accumulated in FP64), rounded once to FP32; p = r.
 // rr_new = |r|^2 of the FP64 residual, rr = |r|^2 of its FP32 copy, bb = |b|^2;
 // conv = 1 when the true residual already meets the tolerance.
+template <bool JAC>
 __global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *__restrict__ b,
                                                         const float *__restrict__ x,
                                                         const double *__restrict__ acc,
+                                                        const float *__restrict__ inv_d,
                                                         float *__restrict__ r, float *__restrict__ p,
                                                         double *partials, double *partials2,
-                                                        double *partials3, CgState *S) {
-    double s_true = 0.0, s_rr = 0.0, s_bb = 0.0;
+                                                        double *partials3, double *partials4, CgState *S) {
+    double s_true = 0.0, s_rr = 0.0, s_bb = 0.0, s_rz = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         const double bi = b[i];
         const double ri = bi - ((double)x[i] + acc[i]);
         const float rf = (float)ri;
         r[i] = rf;
-        p[i] = rf;
+        const float zf = JAC ? rf * inv_d[i] : rf;
+        p[i] = zf;
         s_true += ri * ri;
         s_rr += (double)rf * rf;
         s_bb += bi * bi;
+        if (JAC) s_rz += (double)rf * zf;
     }
     const double pt = block_sum(s_true);
     const double pr = block_sum(s_rr);
     const double pb = block_sum(s_bb);
+    const double pz = block_sum(s_rz);
     if (threadIdx.x == 0) {
         partials2[blockIdx.x] = pr;
         partials3[blockIdx.x] = pb;
+        partials4[blockIdx.x] = pz;
     }
-    double tot;
-    if (finish_reduction(pt, partials, &S->count, tot)) {
-        double rr = 0.0, bb = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) {
-            rr += ((volatile double *)partials2)[k];
-            bb += ((volatile double *)partials3)[k];
-        }
-        S->rr_new = tot;
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = pt;
+        __threadfence();
+        last = atomicAdd(&S->count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, rr = 0.0, bb = 0.0, rz = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += RT) {
+        a += ((volatile double *)partials)[k];
+        rr += ((volatile double *)partials2)[k];
+        bb += ((volatile double *)partials3)[k];
+        rz += ((volatile double *)partials4)[k];
+    }
+    a = block_sum(a);
+    rr = block_sum(rr);
+    bb = block_sum(bb);
+    rz = block_sum(rz);
+    if (threadIdx.x == 0) {
+        S->count = 0;
+        S->rr_new = a;
         S->rr = rr;
+        S->rz = JAC ? rz : rr;
         S->bb = bb;
         S->iters = 0;
-        S->conv = (tot <= S->tol2 * bb) ? 1 : 0;
+        S->conv = (a <= S->tol2 * bb) ? 1 : 0;
     }
 }
 
@@ -90,27 +115,39 @@ __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
         S->pq = tot;
-        S->alpha = S->rr / tot;
+        S->alpha = S->rz / tot;   // rz = rr without preconditioner
     }
 }
 
-// x += alpha p ; r -= alpha q ; rr_new = <r, r> ; beta ; flag
+// x += alpha p ; r -= alpha q ; rr_new = <r, r> (JAC: and <r, z>) ; beta ; flag
+template <bool JAC>
 __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, const float *__restrict__ p,
                                             float *__restrict__ r, const float *__restrict__ q,
-                                            double *partials, CgState *S) {
+                                            const float *__restrict__ inv_d, double *partials,
+                                            double *partials2, CgState *S) {
     if (S->conv) return;
     const float alpha = (float)S->alpha;
-    FFAcc s;
+    FFAcc s, sz;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         x[i] += alpha * p[i];
         float ri = r[i] - alpha * q[i];
         r[i] = ri;
         ff_add_prod(s, ri, ri);
+        if (JAC) ff_add_prod(sz, ri, ri * inv_d[i]);
     }
     double part = block_sum_ff(s);
-    double tot;
-    if (finish_reduction(part, partials, &S->count, tot)) {
-        S->beta = tot / S->rr;
+    double tot, rz = 0.0;
+    bool fin;
+    if (JAC) fin = finish_reduction2(part, block_sum_ff(sz), partials, partials2, &S->count, tot, rz);
+    else fin = finish_reduction(part, partials, &S->count, tot);
+    if (fin) {
+        if (JAC) {
+            S->beta = rz / S->rz;
+            S->rz = rz;
+        } else {
+            S->beta = tot / S->rr;
+            S->rz = tot;
+        }
         S->rr = tot;
         S->iters += 1;
         if (!(tot == tot) || tot > 3.0e38)
@@ -122,13 +159,15 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
     }
 }
 
-// p <- r + beta p ; q <- p
-__global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r,
+// p <- z + beta p (z = r, or r / d) ; q <- p
+template <bool JAC>
+__global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r, const float *__restrict__ inv_d,
                                             float *__restrict__ p, float *__restrict__ q, const CgState *S) {
     if (S->conv) return;
     const float beta = (float)S->beta;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        const float pi = r[i] + beta * p[i];
+        const float zi = JAC ? r[i] * inv_d[i] : r[i];
+        const float pi = zi + beta * p[i];
         p[i] = pi;
         q[i] = pi;
     }
@@ -139,12 +178,13 @@ __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__
 struct CgWorkspace {
     float *r, *p, *q, *z;
     double *acc64;  // aliases q and z (8 bytes per point), used between iterations
-    double *partials, *partials2, *partials3;
+    float *inv_d;   // 1 / (1 + dt A_zz) of the Jacobi-preconditioned solve
+    double *partials, *partials2, *partials3, *partials4;
     CgState *S;
 };
 
 static size_t cg_ws_bytes(int64_t N) {
-    return 4 * (size_t)N * sizeof(float) + 3 * RB * sizeof(double) + 256 + sizeof(CgState);
+    return 5 * (size_t)N * sizeof(float) + 4 * RB * sizeof(double) + 256 + sizeof(CgState);
 }
 
 static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
@@ -161,10 +201,12 @@ static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
     W.q = W.p + s->N;
     W.z = W.q + s->N;
     W.acc64 = (double *)W.q;
-    W.partials = (double *)(W.z + s->N);
+    W.inv_d = W.z + s->N;
+    W.partials = (double *)(W.inv_d + s->N);
     W.partials2 = W.partials + RB;
     W.partials3 = W.partials2 + RB;
-    uintptr_t a = (uintptr_t)(W.partials3 + RB);
+    W.partials4 = W.partials3 + RB;
+    uintptr_t a = (uintptr_t)(W.partials4 + RB);
     a = (a + 255) & ~(uintptr_t)255;
     W.S = (CgState *)a;
     return ADLBR_OK;
@@ -178,9 +220,18 @@ static const int *conv_flag(const CgState *S) {
 // every (re)start measures the true residual b - (I + dt A) x with the
 // operator accumulated in FP64, stops if it meets rtol, and otherwise runs CG
 // on the FP32-rounded residual until the recursive residual meets rtol.
+static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                            int *iters_out, double *relres_out, int every, CgHook hook, void *ctx, bool jac,
+                            cudaStream_t st);
+
 adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                     int *iters_out, double *relres_out, cudaStream_t st) {
-    return run_cg_hooked(s, b, x, dt, rtol, maxit, iters_out, relres_out, 8, nullptr, nullptr, st);
+    return cg_impl(s, b, x, dt, rtol, maxit, iters_out, relres_out, 8, nullptr, nullptr, false, st);
+}
+
+adlbr_status run_pcg_jacobi(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                            int *iters_out, double *relres_out, cudaStream_t st) {
+    return cg_impl(s, b, x, dt, rtol, maxit, iters_out, relres_out, 8, nullptr, nullptr, true, st);
 }
 
 // As run_cg; when hook != NULL it is called (on the host, work enqueued on
@@ -189,9 +240,17 @@ adlbr_status run_cg(adlbr_stencils *s, const float *b, float *x, double dt, doub
 adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
                            int maxit, int *iters_out, double *relres_out, int every, CgHook hook,
                            void *ctx, cudaStream_t st) {
+    return cg_impl(s, b, x, dt, rtol, maxit, iters_out, relres_out, every, hook, ctx, false, st);
+}
+
+static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                            int *iters_out, double *relres_out, int every, CgHook hook, void *ctx, bool jac,
+                            cudaStream_t st) {
     CgWorkspace W;
     if (adlbr_status e = cg_workspace(s, W)) return e;
     const int64_t N = s->N;
+    if (jac)
+        if (adlbr_status e = launch_jacobi_inverse(s, dt, W.inv_d, st)) return e;
     CgState init = {};
     init.tol2 = rtol * rtol;
     CgState host = {};
@@ -204,8 +263,12 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
         ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
         ADLBR_CUDA(cudaMemsetAsync(W.acc64, 0, N * sizeof(double), st));
         if (adlbr_status e = launch_accumulate_f64(s, x, W.acc64, dt, st)) return e;
-        cg_restart_kernel<<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.r, W.p, W.partials, W.partials2,
-                                             W.partials3, W.S);
+        if (jac)
+            cg_restart_kernel<true><<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
+                                                       W.partials2, W.partials3, W.partials4, W.S);
+        else
+            cg_restart_kernel<false><<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
+                                                        W.partials2, W.partials3, W.partials4, W.S);
         ADLBR_CUDA(cudaGetLastError());
         // q = p (q aliases acc64, which the restart kernel has consumed)
         ADLBR_CUDA(cudaMemcpyAsync(W.q, W.p, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -228,8 +291,14 @@ adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double d
                 if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs))
                     return e;
                 cg_k2<<<RB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
-                cg_k3<<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.partials, W.S);
-                cg_k4<<<RB, RT, 0, cs>>>(N, W.r, W.p, W.q, W.S);
+                if (jac) {
+                    cg_k3<true><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
+                    cg_k4<true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                } else {
+                    cg_k3<false><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2,
+                                                    W.S);
+                    cg_k4<false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                }
             }
             ADLBR_CUDA(cudaGetLastError());
             return ADLBR_OK;

@@ -265,6 +265,11 @@ typedef adlbr_status (*CgHook)(void *ctx, const float *r, const float *x, int it
 adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
                            int maxit, int *iters_out, double *relres_out, int every, CgHook hook,
                            void *ctx, cudaStream_t st);
+// CG preconditioned by the diagonal 1 + dt A_zz (same stopping test as run_cg)
+adlbr_status run_pcg_jacobi(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
+                            int *iters_out, double *relres_out, cudaStream_t st);
+// inv_d = 1 / (1 + dt A_zz) (nnpc.cu)
+adlbr_status launch_jacobi_inverse(const adlbr_stencils *s, double dt, float *inv_d, cudaStream_t st);
 // acc += scale * A u (accumulation type: double for F64 u, float otherwise);
 // a kernel launched with skip != NULL returns at once when *skip != 0.
 adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,

@@ -502,6 +502,28 @@ static adlbr_status compute_diag(adlbr_stencils *s, NnWorkspace &W, double dt, d
     return ADLBR_OK;
 }
 
+// 1 / (1 + dt A_zz) per point (the Jacobi preconditioner of the implicit step)
+__global__ void invert_kernel(int64_t N, float *__restrict__ d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) d[i] = 1.f / d[i];
+}
+
+adlbr_status launch_jacobi_inverse(const adlbr_stencils *s, double dt, float *inv_d, cudaStream_t st) {
+    ADLBR_CUDA(cudaMemsetAsync(inv_d, 0, s->N * sizeof(float), st));
+    if (s->dim == 2) {
+        dim3 g(blocks_for(s->n[0], 256), (unsigned)s->n[1]);
+        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs, s->w,
+                                         s->w_t, inv_d);
+    } else {
+        diag3d_kernel<<<dim3(blocks_for(s->n[0], 128), (unsigned)s->n[1], (unsigned)s->n[2]), 128, 0, st>>>(
+            (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (const char4 *)s->offs, s->w, s->w_t, inv_d);
+    }
+    diag_finish_kernel<<<blocks_for(s->N, 256), 256, 0, st>>>(s->N, (float)dt, inv_d, nullptr);
+    invert_kernel<<<blocks_for(s->N, 256), 256, 0, st>>>(s->N, inv_d);
+    ADLBR_CUDA(cudaGetLastError());
+    return ADLBR_OK;
+}
+
 static adlbr_status check_nn_grid(const adlbr_stencils *s, const adlbr_unet *net) {
     if (s->dim != 2) return fail(ADLBR_E_SHAPE, "the learned preconditioner is 2D only");
     if (s->n[0] % (RF * 4) || s->n[1] % (RF * 4))
