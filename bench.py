@@ -414,11 +414,12 @@ def spectral_measurement(n=128, k=7):
             "max_rel_dev": float(np.abs(scaled - cont)[1:].max() / cont[1:].max())}
 
 
-def ced3d_measurement(steps=20):
+def ced3d_measurement(steps=20, precond=2):
     """The 3D coherence-enhancing experiment: 100^3 radial image cos(2 (r/R)^3)
     plus Gaussian noise of variance 0.5 (seed 8), sigma 0.5, rho 4, alpha 1e-2,
     C 1e-5, `steps` steps of dt = 1e-3 on [0,1]^3 (dt = 10 in grid units, so
-    implicit steps): tensor, stencils (F32 weights), CG to 1e-6."""
+    implicit steps): tensor, stencils (F32 weights), CG to 1e-6 (precond 0:
+    plain; 2: preconditioned by the diagonal)."""
     import torch
     import synth
     from paper_1301_3925_gb300 import adlbr as ab
@@ -439,7 +440,7 @@ def ced3d_measurement(steps=20):
             h = ab.adlbr_ced_stencils(h, g, u, scratch, 0.5, 4.0, 1e-2, 1e-5, ab.F32)
             ev[1].record(st)
             x.copy_(u)
-            it, _ = ab.adlbr_step_implicit(h, u, x, dt, 1e-6, 4000)
+            it, _ = ab.adlbr_step_implicit(h, u, x, dt, 1e-6, 4000, precond=precond)
             u.copy_(x)
             ev[2].record(st)
             torch.cuda.synchronize()
@@ -452,7 +453,7 @@ def ced3d_measurement(steps=20):
     ug = u.double().cpu().numpy().reshape(n, n, n)
     rms = lambda a: float(np.sqrt(np.mean(a ** 2)))
     ms = float(np.mean(t_tensor) + np.mean(t_solve))
-    return {"grid": [n, n, n], "steps": steps, "dt_grid_units": dt,
+    return {"grid": [n, n, n], "steps": steps, "dt_grid_units": dt, "precond": precond,
             "ms_per_step": ms, "tensor_and_stencils_ms": float(np.mean(t_tensor)),
             "implicit_ms": float(np.mean(t_solve)), "cg_iters_mean": float(np.mean(iters)),
             "gpts_per_step": n ** 3 / (ms * 1e-3) / 1e9,
@@ -778,7 +779,11 @@ def main():
     implicit = None if args.no_implicit or rank != 0 else implicit_measurement(peak)
     volume = None if args.no_3d or rank != 0 else volume_measurement(peak, args.precision_steps)
     batch = None if args.no_batch or rank != 0 else batch_measurement(peak)
-    ced3d = None if args.no_ced3d or rank != 0 else ced3d_measurement()
+    ced3d = None
+    if not args.no_ced3d and rank == 0:
+        ced3d = ced3d_measurement(precond=2)
+        plain = ced3d_measurement(precond=0)
+        ced3d["plain_cg"] = {k: plain[k] for k in ("ms_per_step", "implicit_ms", "cg_iters_mean", "rms_to_clean")}
     spectral_study = None if args.no_spectral or rank != 0 else spectral_measurement()
 
     cpu = None
