@@ -86,3 +86,19 @@ def test_single_point_grid():
         assert Au.item() == 0.0 and u.item() == 0.75
     finally:
         ab.adlbr_stencils_destroy(h)
+
+
+def test_stencils_grid_round_trip():
+    """adlbr_stencils_grid returns the grid the handle was built on."""
+    t = torch()
+    for shape, bc in (((12, 20), ab.NEUMANN), ((6, 8, 10), ab.PERIODIC)):
+        # D = identity: planes (Dxx, Dxy, Dyy) or (Dxx, Dyy, Dzz, Dxy, Dxz, Dyz)
+        diag = [1.0, 0.0, 1.0] if len(shape) == 2 else [1.0, 1.0, 1.0, 0.0, 0.0, 0.0]
+        D = np.array(diag).reshape(-1, 1) * np.ones((1, int(np.prod(shape))))
+        h = ab.adlbr_build_stencils(ab.grid(shape, bc), dev(D, t.float64), ab.F64, ab.F32)
+        try:
+            g = ab.adlbr_stencils_grid(h)
+            assert g.dim == len(shape) and g.bc == bc
+            assert tuple(int(g.n[k]) for k in range(len(shape))) == tuple(reversed(shape))
+        finally:
+            ab.adlbr_stencils_destroy(h)

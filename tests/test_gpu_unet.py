@@ -127,3 +127,19 @@ def test_unet_tensor_cores_reject_unsupported_widths():
             ab.adlbr_unet_set_tensor_cores(net, True)
     finally:
         ab.adlbr_unet_destroy(net)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 1 << 20])
+def test_mse_grad_matches_formula(n):
+    """adlbr_mse_grad: loss = mean((y - t)^2) (FP64 reduction), gy = 2 (y - t) / n."""
+    t = torch()
+    g = np.random.default_rng(n)
+    y, tt = g.normal(size=n), g.normal(size=n)
+    yd, td = dev(y, t.float32), dev(tt, t.float32)
+    gy = t.empty_like(yd)
+    loss = ab.adlbr_mse_grad(yd, td, n, gy)
+    t.cuda.synchronize()
+    y32, t32 = y.astype(np.float32).astype(np.float64), tt.astype(np.float32).astype(np.float64)
+    d = y32 - t32
+    assert abs(loss - np.mean(d * d)) <= 1e-6 * max(1.0, np.mean(d * d))
+    assert np.abs(gy.double().cpu().numpy() - 2 * d / n).max() <= 1e-6 * (2 * np.abs(d).max() / n)
