@@ -17,7 +17,7 @@ RF = 4         # restriction factor of the preconditioner
 
 
 def generate_pairs(h, rhs, dt, rtol=1e-6, maxit=4000, every=4, max_pairs=48, precond=None):
-    """Solver-generated pairs for the stencils h: returns (feats [n,10,Hc,Wc],
+    """Solver-generated pairs for the stencils h: returns (feats [n,NF,Hc,Wc],
     targets [n,Hc,Wc]) as CUDA tensors.  precond (a Preconditioner) makes the
     recording solve the preconditioned one, so the pairs follow its residuals."""
     import torch
@@ -131,7 +131,7 @@ def train(feats, targets, steps=400, batch=8, crop=64, lr=2e-3, seed=0, c=(16, 3
 class Preconditioner:
     """The trained network instantiated for a full-size grid (batch 1); its
     forward convolutions run on the tensor cores unless tensor_cores=False
-    (BF16 operands, FP32 accumulation; 0.42 ms against 0.97 ms for the FP32
+    (BF16 operands, FP32 accumulation; 0.26 ms against 0.97 ms for the FP32
     kernels at 512^2)."""
 
     def __init__(self, params, nx, ny, c=(16, 32, 64), tensor_cores=True):
