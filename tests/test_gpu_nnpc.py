@@ -36,12 +36,13 @@ def _params(seed, scale_out=1.0):
     return th
 
 
-def test_precondition_matches_oracle():
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_precondition_matches_oracle(tensor_cores):
     t = torch()
     shape = (64, 96)
     h, oo, ow, diag, dt = _problem(shape, 5)
     theta = _params(1)
-    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0], tensor_cores=False)
+    pc = nn.Preconditioner(dev(theta, t.float32), shape[1], shape[0], tensor_cores=tensor_cores)
     try:
         r = synth.u_uniform(shape, 6) - 0.5
         rd = dev(r.ravel(), t.float32)
@@ -54,7 +55,13 @@ def test_precondition_matches_oracle():
     th32 = theta.astype(np.float32).astype(np.float64)
     r32 = r.astype(np.float32).astype(np.float64)
     zo = ou.precondition(th32, oo, ow, dt, diag, r32)
-    assert np.abs(zg - zo).max() <= 2e-4 * np.abs(zo).max()
+    if not tensor_cores:
+        assert np.abs(zg - zo).max() <= 2e-4 * np.abs(zo).max()
+        return
+    # BF16 network: the Jacobi part r / d stays FP32; the error is bounded by
+    # the forward's tolerance on the network's own term s P(y)
+    net_part = zo - r32 / (1.0 + dt * diag)
+    assert np.abs(zg - zo).max() <= 3e-2 * np.abs(net_part).max() + 2e-4 * np.abs(zo).max()
 
 
 def test_training_pairs_match_oracle_features():
