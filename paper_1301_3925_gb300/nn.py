@@ -131,7 +131,7 @@ def train(feats, targets, steps=400, batch=8, crop=64, lr=2e-3, seed=0, c=(16, 3
 class Preconditioner:
     """The trained network instantiated for a full-size grid (batch 1); its
     forward convolutions run on the tensor cores unless tensor_cores=False
-    (BF16 operands, FP32 accumulation; 0.26 ms against 0.97 ms for the FP32
+    (BF16 operands, FP32 accumulation; 0.245 ms against 0.97 ms for the FP32
     kernels at 512^2)."""
 
     def __init__(self, params, nx, ny, c=(16, 32, 64), tensor_cores=True):
