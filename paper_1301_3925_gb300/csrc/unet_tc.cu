@@ -338,20 +338,6 @@ adlbr_status launch_tc(int B, int H, int W, const ConvMaps &maps, int g0, int kp
 // ---- the layers around the convolutions (BF16, channels last) ------------
 
 // FP32 [B][C][HW] -> BF16 [B][HW][Cp], channels C .. Cp - 1 zero
-__global__ void to_nhwc_kernel(int B, int C, int Cp, int64_t HW, const float *__restrict__ x,
-                               __nv_bfloat16 *__restrict__ y) {
-    const int64_t n = (int64_t)B * HW * (Cp / 2);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c2 = (int)(i % (Cp / 2));
-        const int64_t p = i / (Cp / 2);
-        const int64_t b = p / HW, q = p % HW;
-        const int c = 2 * c2;
-        const float v0 = c < C ? x[(b * C + c) * HW + q] : 0.f;
-        const float v1 = c + 1 < C ? x[(b * C + c + 1) * HW + q] : 0.f;
-        reinterpret_cast<__nv_bfloat162 *>(y)[i] = __floats2bfloat162_rn(v0, v1);
-    }
-}
-
 __device__ __forceinline__ void unpack8(const uint4 &r, float (&f)[8]) {
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
 #pragma unroll
@@ -367,6 +353,26 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
     return r;
+}
+
+// One thread per pixel: the C plane reads of a warp are 32 consecutive floats
+// each, and the pixel's Cp channels (a multiple of 8) go out as 16-byte
+// stores.  (Two channels per thread, with lanes across channels, read 8 bytes
+// of each 32-byte sector and took 21 us at 512^2, 25 -> 32 channels.)
+__global__ void to_nhwc_kernel(int B, int C, int Cp, int64_t HW, const float *__restrict__ x,
+                               __nv_bfloat16 *__restrict__ y) {
+    const int64_t n = (int64_t)B * HW;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = p / HW, q = p - b * HW;
+        const float *xs = x + b * C * HW + q;
+        uint4 *d = reinterpret_cast<uint4 *>(y + p * Cp);
+        for (int c0 = 0; c0 < Cp; c0 += 8) {
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = c0 + k < C ? xs[(int64_t)(c0 + k) * HW] : 0.f;
+            d[c0 / 8] = pack8(f);
+        }
+    }
 }
 
 // 2 x 2 average pooling: [B][2H2][2W2][C] -> [B][H2][W2][C], 8 channels a thread
@@ -464,7 +470,7 @@ adlbr_status conv_tc(int B, int H, int W, const __nv_bfloat16 *x0, int C0, const
 }
 
 adlbr_status tc_to_nhwc(int B, int C, int Cp, int64_t HW, const float *x, __nv_bfloat16 *y, cudaStream_t st) {
-    to_nhwc_kernel<<<grid_for((int64_t)B * HW * Cp / 2), 256, 0, st>>>(B, C, Cp, HW, x, y);
+    to_nhwc_kernel<<<grid_for((int64_t)B * HW), 256, 0, st>>>(B, C, Cp, HW, x, y);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
