@@ -65,6 +65,9 @@ def parse():
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
     p.add_argument("--profile-unet", action="store_true",
                    help="only run four tensor-core U-Net forwards at 512^2 (for ncu launch lists)")
+    p.add_argument("--profile-fcg", action="store_true",
+                   help="only run two 40-iteration flexible-CG solves with the U-Net preconditioner "
+                        "at 2048^2 (for ncu launch lists)")
     return p.parse_args()
 
 
@@ -318,6 +321,45 @@ def profile_cg():
     torch.cuda.synchronize()
     ab.adlbr_stencils_destroy(h)
     print(json.dumps({"profile_cg": {"iters": it, "relres": rel}}))
+    return 0
+
+
+def profile_fcg():
+    """Two flexible-CG solves of the 2048^2 implicit step with the tensor-core
+    U-Net preconditioner, stopped after 40 iterations (profiling entry).  The
+    network is untrained (He-normal weights, output layer scaled by 1e-3):
+    an iteration runs the same kernels as with trained weights."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    from paper_1301_3925_gb300 import nn
+    n = 2048
+    D = torch.from_numpy(synth.smooth_field2d(n, n, 3, 1.0, 50.0, 16).reshape(3, -1)
+                         .astype(np.float32)).cuda()
+    g = ab.grid((n, n))
+    h = ab.adlbr_build_stencils(g, D, ab.F32, ab.F32)
+    dt = 200.0 / ab.adlbr_stencils_max_diag(h)
+    b = torch.from_numpy(synth.u_uniform((n, n), 3).astype(np.float32).ravel()).cuda()
+    x = torch.empty_like(b)
+    shapes = nn.layer_shapes(nn.NF, 16, 32, 64)
+    th = nn.init_params(sum(co * ci * k * k + co for co, ci, k in shapes), shapes, 1)
+    th[-17:] *= 1e-3   # output layer (16 weights + bias)
+    pc = nn.Preconditioner(torch.from_numpy(th).cuda(), n, n)
+    out = []
+    try:
+        for _ in range(2):
+            x.copy_(b)
+            try:
+                out.append(ab.adlbr_step_implicit(h, b, x, dt, 1e-6, 40, precond=1, nn=pc.desc))
+            except ab.AdlbrError as e:   # E_NOT_CONVERGED after 40 iterations
+                out.append(str(e).split(":")[0])
+        torch.cuda.synchronize()
+    finally:
+        pc.close()
+        ab.adlbr_stencils_destroy(h)
+    print(json.dumps({"profile_fcg": {"solves": [str(o) for o in out]}}))
     return 0
 
 
@@ -619,6 +661,8 @@ def main():
         return profile_cg()
     if args.profile_unet:
         return profile_unet()
+    if args.profile_fcg:
+        return profile_fcg()
 
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
