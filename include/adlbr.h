@@ -139,6 +139,9 @@ adlbr_status adlbr_stencils_destroy(adlbr_stencils *s);
  *  u    device, N elements of u_t (F64, F32, F16 or BF16).
  *  Au   device, N elements: double when u_t == ADLBR_F64, float otherwise
  *       (accumulation is in that type).  Must not alias u.
+ * The transpose terms are added with atomic operations, so the rounding of
+ * Au (and of the solvers built on it) can differ in the last bits from run to
+ * run; the dot products and norms of the solvers reduce in a fixed order.
  */
 adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                          cudaStream_t stream);

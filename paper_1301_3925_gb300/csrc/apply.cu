@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, floa
                                                     const void *__restrict__ wbase, adlbr_dtype wt,
                                                     const UT *__restrict__ u, float *__restrict__ acc,
                                                     const int *__restrict__ skip) {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
     op::tile2d<UT, TW, TH, NT, WX, F16W>(nx, ny, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TW,
                                          blockIdx.y * TH, smem);
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled(int nx, int ny, int 
                                                          const void *__restrict__ wbase, adlbr_dtype wt,
                                                          const UT *__restrict__ u, float *__restrict__ acc,
                                                          const int *__restrict__ skip) {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
     op::tile3d<UT, TX, TY, TZ, F16W>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
                                      blockIdx.y * TY, blockIdx.z * TZ, smem);

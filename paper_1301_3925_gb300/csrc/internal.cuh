@@ -229,6 +229,12 @@ adlbr_status unet_adam(float *params, const float *grads, float *m, float *v, in
                        double b1, double b2, double eps, int t, cudaStream_t st);
 int64_t unet_num_params(const adlbr_unet *n);
 adlbr_status unet_set_tensor_cores(adlbr_unet *n, int on);
+// The tensor-core forward's BF16 channels-last input buffer ([B][H][W][cp],
+// cp = cin rounded up to 16), or nullptr when the network runs on FP32 cores;
+// unet_forward_from_input runs the tensor-core forward on it as it stands
+// (a caller can keep channels that do not change between forwards there).
+__nv_bfloat16 *unet_tc_input(adlbr_unet *n, int *cp);
+adlbr_status unet_forward_from_input(adlbr_unet *n, const float *params, float *yout, cudaStream_t st);
 // tensor-core 3x3 convolution + bias + ReLU (unet_tc.cu)
 size_t conv_tc_pack_elems(int Co, int Ci);
 struct ConvPackTable {   // the 3x3 layers packed by one conv_tc_pack launch

@@ -186,6 +186,55 @@ __global__ void coarse_r_kernel(int nx, int ny, const float *__restrict__ r, con
                 r[(int64_t)(cy * RF + dy) * nx + cx * RF + dx] * inv;
 }
 
+// The same two feature sets written straight into the tensor-core network's
+// BF16 channels-last input x ([Hc][Wc][cp]), with the rounding of its own
+// conversion (FP32 feature, then round to nearest BF16):
+// channels 0 .. NR-1 = r / s per block (every iteration; four 16-byte row
+// reads, two 16-byte stores per coarse point) ...
+__global__ void coarse_r_nhwc_kernel(int nx, int ny, const float *__restrict__ r, const FcgState *S, int64_t N,
+                                     int cp, __nv_bfloat16 *__restrict__ xh) {
+    static_assert(RF == 4 && NR == 16, "one float4 per block row, two 8-channel stores");
+    if (S->conv) return;
+    const int Wc = nx / RF, Hc = ny / RF;
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y;
+    if (cx >= Wc || cy >= Hc) return;
+    const double s = sqrt(S->rr / (double)N);
+    const float inv = s > 0.0 ? (float)(1.0 / s) : 0.f;
+    float f[NR];
+#pragma unroll
+    for (int dy = 0; dy < RF; ++dy) {
+        const float4 v = *reinterpret_cast<const float4 *>(r + (int64_t)(cy * RF + dy) * nx + cx * RF);
+        f[dy * RF + 0] = v.x * inv;
+        f[dy * RF + 1] = v.y * inv;
+        f[dy * RF + 2] = v.z * inv;
+        f[dy * RF + 3] = v.w * inv;
+    }
+    uint4 o[2];
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(o);
+#pragma unroll
+    for (int k = 0; k < NR / 2; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+    uint4 *d = reinterpret_cast<uint4 *>(xh + ((int64_t)cy * Wc + cx) * cp);
+    d[0] = o[0];
+    d[1] = o[1];
+}
+
+// ... and channels NR .. cp-1 = the static features, then zeros (once per solve).
+__global__ void static_nhwc_kernel(int64_t Nc, int cp, const float *__restrict__ feat,
+                                   __nv_bfloat16 *__restrict__ xh) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Nc; q += (int64_t)gridDim.x * blockDim.x) {
+        for (int c0 = NR; c0 < cp; c0 += 8) {
+            uint4 o;
+            __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&o);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c0 + 2 * k;
+                h[k] = __floats2bfloat162_rn(c < NF ? feat[c * Nc + q] : 0.f, c + 1 < NF ? feat[(c + 1) * Nc + q] : 0.f);
+            }
+            reinterpret_cast<uint4 *>(xh + q * cp)[c0 / 8] = o;
+        }
+    }
+}
+
 // r = b - (x + q) (q = dt A x), rr, bb.  As in the CG kernels, no kernel
 // here stores a constant over a value it has just loaded; q receives p in
 // the kernels that produce p, and the operator accumulates dt A p into it.
@@ -314,26 +363,22 @@ __global__ void __launch_bounds__(RT) fcg_z2_kernel(int64_t N, const float *__re
     }
 }
 
-// p = z + beta p ; q = Az + beta q   (first: p = z, q = Az)
+// p = z + beta p ; q = Az + beta q   (first: p = z, q = Az), then
+// alpha = rz / <p, q> from the values just written (q = p + dt A p)
 template <bool FIRST>
-__global__ void fcg_p2_kernel(int64_t N, const float *__restrict__ z, const float *__restrict__ Az,
-                              float *__restrict__ p, float *__restrict__ q, const FcgState *S) {
+__global__ void __launch_bounds__(RT) fcg_p2_kernel(int64_t N, const float *__restrict__ z,
+                                                    const float *__restrict__ Az, float *__restrict__ p,
+                                                    float *__restrict__ q, double *partials, FcgState *S) {
     if (S->conv) return;
     const float beta = FIRST ? 0.f : (float)S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        p[i] = FIRST ? z[i] : fmaf(beta, p[i], z[i]);
-        q[i] = FIRST ? Az[i] : fmaf(beta, q[i], Az[i]);
-    }
-}
-
-// alpha = rz / <p, q>   (q = p + dt A p)
-__global__ void __launch_bounds__(RT) fcg_q_kernel(int64_t N, const float *__restrict__ p,
-                                                   const float *__restrict__ q, double *partials, FcgState *S) {
-    if (S->conv) return;
     FFAcc s;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
-        ff_add_prod(s, p[i], q[i]);
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
+        const float pi = FIRST ? z[i] : fmaf(beta, p[i], z[i]);
+        const float qi = FIRST ? Az[i] : fmaf(beta, q[i], Az[i]);
+        p[i] = pi;
+        q[i] = qi;
+        ff_add_prod(s, pi, qi);
+    }
     double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
@@ -577,15 +622,22 @@ static adlbr_status galerkin_direction(adlbr_stencils *s, NnWorkspace &W, adlbr_
     const int nx = (int)s->n[0], ny = (int)s->n[1];
     const int64_t N = s->N;
     dim3 gc(blocks_for(nx / RF, 128), (unsigned)(ny / RF));
-    coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, W.feat);
-    if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
+    int cp = 0;
+    if (__nv_bfloat16 *xh = unet_tc_input(net, &cp)) {
+        // the static channels were written at the start of the solve
+        coarse_r_nhwc_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, cp, xh);
+        if (adlbr_status e = unet_forward_from_input(net, params, W.y, st)) return e;
+    } else {
+        coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, W.feat);
+        if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
+    }
     fcg_w_kernel<<<NB, RT, 0, st>>>(nx, N, W.r, W.d, W.y, W.z, W.c, W.g1, W.g2, W.S);
     if (adlbr_status e = launch_accumulate(s, W.z, W.g1, ADLBR_F32, dt, skip, st)) return e;
     if (adlbr_status e = launch_accumulate(s, W.c, W.g2, ADLBR_F32, dt, skip, st)) return e;
     fcg_gamma_kernel<<<NB, RT, 0, st>>>(N, W.r, W.c, W.g1, W.g2, W.partials, W.partials2, W.S);
     fcg_z2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.r, W.r_old, W.z, W.c, W.g1, W.g2, W.partials, W.partials2,
                                             W.S);
-    fcg_p2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.z, W.g1, W.p, W.q, W.S);
+    fcg_p2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.z, W.g1, W.p, W.q, W.partials, W.S);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
@@ -606,6 +658,14 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     const int64_t N = s->N;
     if (adlbr_status e = compute_diag(s, W, dt, nullptr, st)) return e;
     static_features(s, W, dt, st);
+    {   // tensor-core network: its input buffer keeps the static channels
+        int cp = 0;
+        if (__nv_bfloat16 *xh = unet_tc_input(nn->net, &cp)) {
+            const int64_t Nc = N / (RF * RF);
+            static_nhwc_kernel<<<(unsigned)std::min<int64_t>((Nc + 255) / 256, 152 * 8), 256, 0, st>>>(Nc, cp, W.feat,
+                                                                                                     xh);
+        }
+    }
     FcgState init = {};
     init.tol2 = rtol * rtol;
     init.max_iters = maxit;
@@ -633,8 +693,8 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     bool fall_back = false;
     auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
         for (int k = 0; k < chunk; ++k) {
-            // q = (I + dt A) p is carried by the recurrences: no operator here
-            fcg_q_kernel<<<NB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
+            // q = (I + dt A) p is carried by the recurrences (no operator
+            // here) and alpha was set with p and q
             fcg_x_kernel<<<NB, RT, 0, cs>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
             if (adlbr_status e = galerkin_direction<false>(s, W, nn->net, nn->params, dt, skip, cs)) return e;
         }

@@ -380,13 +380,15 @@ adlbr_status conv3x3_bwd(const adlbr_unet *n, const Layer &L, int H, int W, cons
 
 }  // namespace
 
-adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, float *yout,
-                          cudaStream_t st) {
+namespace {
+
+// The tensor-core forward from the BF16 channels-last input n->hx.
+adlbr_status tc_forward(adlbr_unet *n, const float *params, float *yout, cudaStream_t st) {
     Layer L[11];
     layer_table(n, L);
     const int H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int B = n->B;
-    if (n->tensor_cores) {
+    {
         ConvPackTable T;
         T.n = 10;
         for (int l = 0; l < 10; ++l) {
@@ -403,7 +405,6 @@ adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, 
             return conv_tc(B, h, w, x0, C0, x1, C1, L[l].co, n->wpack + n->wpack_off[l], params + L[l].b_off, y,
                            st);
         };
-        if (adlbr_status e = tc_to_nhwc(B, n->cin, cp, (int64_t)H * W, xin, n->hx, st)) return e;
         if (adlbr_status e = cv(0, H, W, n->hx, cp, nullptr, 0, n->h1a)) return e;
         if (adlbr_status e = cv(1, H, W, n->h1a, c1, nullptr, 0, n->h1b)) return e;
         if (adlbr_status e = tc_pool(B, H2, W2, c1, n->h1b, n->hp1, st)) return e;
@@ -424,6 +425,32 @@ adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, 
             return e;
         ADLBR_CUDA(cudaGetLastError());
         return ADLBR_OK;
+    }
+}
+
+}  // namespace
+
+__nv_bfloat16 *unet_tc_input(adlbr_unet *n, int *cp) {
+    if (!n->tensor_cores) return nullptr;
+    *cp = (n->cin + 15) / 16 * 16;
+    return n->hx;
+}
+
+adlbr_status unet_forward_from_input(adlbr_unet *n, const float *params, float *yout, cudaStream_t st) {
+    if (!n->tensor_cores) return fail(ADLBR_E_ARG, "the network's input buffer needs the tensor-core forward");
+    return tc_forward(n, params, yout, st);
+}
+
+adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, float *yout,
+                          cudaStream_t st) {
+    Layer L[11];
+    layer_table(n, L);
+    const int H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int B = n->B;
+    if (n->tensor_cores) {
+        const int cp = (n->cin + 15) / 16 * 16;
+        if (adlbr_status e = tc_to_nhwc(B, n->cin, cp, (int64_t)H * W, xin, n->hx, st)) return e;
+        return tc_forward(n, params, yout, st);
     }
     n->fwd_tc = 0;
     auto cr = [&](int l, int h, int w, const float *x, float *y) {
