@@ -230,10 +230,13 @@ adlbr_status unet_adam(float *params, const float *grads, float *m, float *v, in
 int64_t unet_num_params(const adlbr_unet *n);
 adlbr_status unet_set_tensor_cores(adlbr_unet *n, int on);
 // The tensor-core forward's BF16 channels-last input buffer ([B][H][W][cp],
-// cp = cin rounded up to 16), or nullptr when the network runs on FP32 cores;
-// unet_forward_from_input runs the tensor-core forward on it as it stands
-// (a caller can keep channels that do not change between forwards there).
+// cp = cin rounded up to 16), or nullptr when the network runs on FP32 cores.
+// unet_tc_prepare packs the BF16 weights of params; unet_forward_from_input
+// then runs the tensor-core forward on the input buffer and the packed
+// weights as they stand (a caller whose parameters and some input channels
+// do not change between forwards sets them up once).
 __nv_bfloat16 *unet_tc_input(adlbr_unet *n, int *cp);
+adlbr_status unet_tc_prepare(adlbr_unet *n, const float *params, cudaStream_t st);
 adlbr_status unet_forward_from_input(adlbr_unet *n, const float *params, float *yout, cudaStream_t st);
 // tensor-core 3x3 convolution + bias + ReLU (unet_tc.cu)
 size_t conv_tc_pack_elems(int Co, int Ci);

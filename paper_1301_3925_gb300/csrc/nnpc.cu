@@ -624,7 +624,8 @@ static adlbr_status galerkin_direction(adlbr_stencils *s, NnWorkspace &W, adlbr_
     dim3 gc(blocks_for(nx / RF, 128), (unsigned)(ny / RF));
     int cp = 0;
     if (__nv_bfloat16 *xh = unet_tc_input(net, &cp)) {
-        // the static channels were written at the start of the solve
+        // the static channels and the packed weights were set up at the start
+        // of the solve
         coarse_r_nhwc_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, cp, xh);
         if (adlbr_status e = unet_forward_from_input(net, params, W.y, st)) return e;
     } else {
@@ -658,12 +659,14 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
     const int64_t N = s->N;
     if (adlbr_status e = compute_diag(s, W, dt, nullptr, st)) return e;
     static_features(s, W, dt, st);
-    {   // tensor-core network: its input buffer keeps the static channels
+    {   // tensor-core network: its input buffer keeps the static channels and
+        // its packed weights stay for the whole solve
         int cp = 0;
         if (__nv_bfloat16 *xh = unet_tc_input(nn->net, &cp)) {
             const int64_t Nc = N / (RF * RF);
             static_nhwc_kernel<<<(unsigned)std::min<int64_t>((Nc + 255) / 256, 152 * 8), 256, 0, st>>>(Nc, cp, W.feat,
                                                                                                      xh);
+            if (adlbr_status e = unet_tc_prepare(nn->net, nn->params, st)) return e;
         }
     }
     FcgState init = {};

@@ -383,21 +383,31 @@ adlbr_status conv3x3_bwd(const adlbr_unet *n, const Layer &L, int H, int W, cons
 namespace {
 
 // The tensor-core forward from the BF16 channels-last input n->hx.
-adlbr_status tc_forward(adlbr_unet *n, const float *params, float *yout, cudaStream_t st) {
+// The BF16 operand copies of the ten 3x3 layers' weights (n->wpack).
+adlbr_status tc_pack(adlbr_unet *n, const float *params, cudaStream_t st) {
+    Layer L[11];
+    layer_table(n, L);
+    ConvPackTable T;
+    T.n = 10;
+    for (int l = 0; l < 10; ++l) {
+        T.co[l] = L[l].co;
+        T.ci[l] = L[l].ci;
+        T.w_off[l] = L[l].w_off;
+        T.out_off[l] = (int64_t)n->wpack_off[l];
+    }
+    return conv_tc_pack(T, params, n->wpack, st);
+}
+
+// The tensor-core forward from the BF16 channels-last input n->hx and the
+// packed weights n->wpack (packed here when `pack`).
+adlbr_status tc_forward(adlbr_unet *n, const float *params, float *yout, bool pack, cudaStream_t st) {
     Layer L[11];
     layer_table(n, L);
     const int H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int B = n->B;
     {
-        ConvPackTable T;
-        T.n = 10;
-        for (int l = 0; l < 10; ++l) {
-            T.co[l] = L[l].co;
-            T.ci[l] = L[l].ci;
-            T.w_off[l] = L[l].w_off;
-            T.out_off[l] = (int64_t)n->wpack_off[l];
-        }
-        if (adlbr_status e = conv_tc_pack(T, params, n->wpack, st)) return e;
+        if (pack)
+            if (adlbr_status e = tc_pack(n, params, st)) return e;
         n->fwd_tc = 1;
         const int c1 = n->c1, c2 = n->c2, c3 = n->c3, cp = (n->cin + 15) / 16 * 16;
         auto cv = [&](int l, int h, int w, const __nv_bfloat16 *x0, int C0, const __nv_bfloat16 *x1, int C1,
@@ -436,9 +446,14 @@ __nv_bfloat16 *unet_tc_input(adlbr_unet *n, int *cp) {
     return n->hx;
 }
 
+adlbr_status unet_tc_prepare(adlbr_unet *n, const float *params, cudaStream_t st) {
+    if (!n->tensor_cores) return fail(ADLBR_E_ARG, "the packed weights need the tensor-core forward");
+    return tc_pack(n, params, st);
+}
+
 adlbr_status unet_forward_from_input(adlbr_unet *n, const float *params, float *yout, cudaStream_t st) {
     if (!n->tensor_cores) return fail(ADLBR_E_ARG, "the network's input buffer needs the tensor-core forward");
-    return tc_forward(n, params, yout, st);
+    return tc_forward(n, params, yout, false, st);
 }
 
 adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, float *yout,
@@ -450,7 +465,7 @@ adlbr_status unet_forward(adlbr_unet *n, const float *params, const float *xin, 
     if (n->tensor_cores) {
         const int cp = (n->cin + 15) / 16 * 16;
         if (adlbr_status e = tc_to_nhwc(B, n->cin, cp, (int64_t)H * W, xin, n->hx, st)) return e;
-        return tc_forward(n, params, yout, st);
+        return tc_forward(n, params, yout, true, st);
     }
     n->fwd_tc = 0;
     auto cr = [&](int l, int h, int w, const float *x, float *y) {
