@@ -239,6 +239,10 @@ __device__ __forceinline__ void blur_group(const float (&v)[NB + 2 * RR], const 
 }
 
 constexpr int RBY = 8;   // rows per thread in the last (y) pass: 512 groups
+// outputs per thread in the first three passes of the fused kernel: 8 reads
+// 2r + 8 staged values per 8 outputs (0.267 against 0.286 ms with 4 at
+// 4096^2, sigma 1, rho 4; 16 in the P x pass alone: 0.269)
+constexpr int RBF = 8;
 
 // S_, R_ > 0: radii fixed at compile time (all loops unrolled, windows in
 // registers, constant index arithmetic); 0: taken from g at run time, with
@@ -312,35 +316,35 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         origin(tile + gridDim.x, nx0, ny0);
         load_u_window<S_, R_>(g, nx, ny, nx0, ny0, u, (it & 1) ? sm : sm + g.offU1);
     }
-    // 2. bx = x pass of u (lanes along rows, RB outputs per thread)
+    // 2. bx = x pass of u (lanes along rows, RBF outputs per thread)
     {
-        const int groups = (g.BW + RB - 1) / RB;
+        const int groups = (g.BW + RBF - 1) / RBF;
         for (int i = threadIdx.x; i < g.BH * groups; i += FNT) {
-            const int r = i % g.BH, c0 = (i / g.BH) * RB;
+            const int r = i % g.BH, c0 = (i / g.BH) * RBF;
             const float *s = U + r * g.UP + c0 + S - SR;
-            float v[RB + 2 * SR], acc[RB];
+            float v[RBF + 2 * SR], acc[RBF];
 #pragma unroll
-            for (int j = 0; j < RB + 2 * SR; ++j) v[j] = (fixed || (j >= SR - S && j < SR + S + RB)) ? s[j] : 0.f;
-            blur_group<SR>(v, ts, S, acc);
+            for (int j = 0; j < RBF + 2 * SR; ++j) v[j] = (fixed || (j >= SR - S && j < SR + S + RBF)) ? s[j] : 0.f;
+            blur_group<SR, RBF>(v, ts, S, acc);
 #pragma unroll
-            for (int o = 0; o < RB; ++o)
+            for (int o = 0; o < RBF; ++o)
                 if (c0 + o < g.BW) B[r * g.BP + c0 + o] = acc[o];
         }
     }
     __syncthreads();
-    // 3. u_sigma = y pass of bx (lanes along columns, RB rows per thread)
+    // 3. u_sigma = y pass of bx (lanes along columns, RBF rows per thread)
     {
-        const int groups = (g.SH + RB - 1) / RB;
+        const int groups = (g.SH + RBF - 1) / RBF;
         for (int i = threadIdx.x; i < g.SW * groups; i += FNT) {
-            const int c = i % g.SW, r0 = (i / g.SW) * RB;
+            const int c = i % g.SW, r0 = (i / g.SW) * RBF;
             const float *s = B + (r0 + S - SR) * g.BP + c;
-            float v[RB + 2 * SR], acc[RB];
+            float v[RBF + 2 * SR], acc[RBF];
 #pragma unroll
-            for (int j = 0; j < RB + 2 * SR; ++j)
-                v[j] = (fixed || (j >= SR - S && j < SR + S + RB)) ? s[j * g.BP] : 0.f;
-            blur_group<SR>(v, ts, S, acc);
+            for (int j = 0; j < RBF + 2 * SR; ++j)
+                v[j] = (fixed || (j >= SR - S && j < SR + S + RBF)) ? s[j * g.BP] : 0.f;
+            blur_group<SR, RBF>(v, ts, S, acc);
 #pragma unroll
-            for (int o = 0; o < RB; ++o)
+            for (int o = 0; o < RBF; ++o)
                 if (r0 + o < g.SH) US[(r0 + o) * g.SP + c] = acc[o];
         }
     }
@@ -360,19 +364,19 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
     __syncthreads();
     // 5. Px = x pass of P over the FT output columns (lanes along rows)
     {
-        constexpr int groups = FT / RB;
+        constexpr int groups = FT / RBF;
         for (int i = threadIdx.x; i < g.PH * groups; i += FNT) {
-            const int r = i % g.PH, c0 = (i / g.PH) * RB;
+            const int r = i % g.PH, c0 = (i / g.PH) * RBF;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float *s = P + (ch * g.PH + r) * g.PP + c0 + R - RR;
-                float v[RB + 2 * RR], acc[RB];
+                float v[RBF + 2 * RR], acc[RBF];
 #pragma unroll
-                for (int j = 0; j < RB + 2 * RR; ++j)
-                    v[j] = (fixed || (j >= RR - R && j < RR + R + RB)) ? s[j] : 0.f;
-                blur_group<RR>(v, tr, R, acc);
+                for (int j = 0; j < RBF + 2 * RR; ++j)
+                    v[j] = (fixed || (j >= RR - R && j < RR + R + RBF)) ? s[j] : 0.f;
+                blur_group<RR, RBF>(v, tr, R, acc);
 #pragma unroll
-                for (int o = 0; o < RB; ++o) PX[(ch * g.PH + r) * g.XP + c0 + o] = acc[o];
+                for (int o = 0; o < RBF; ++o) PX[(ch * g.PH + r) * g.XP + c0 + o] = acc[o];
             }
         }
     }
