@@ -42,7 +42,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch at 4096^2, from an ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum, one launch each,
 # second warm-up step of this benchmark's CED step)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.180e6 + 140.324e6, "build2d_kernel": 201.348e6 + 229.138e6,
+TRAFFIC_4096 = {"ced_fused_kernel": 67.183e6 + 140.391e6, "build2d_kernel": 201.348e6 + 229.138e6,
                 # operator + finalize
                 "explicit_step": 402.735e6 + 51.184e6 + 134.225e6 + 21.878e6}
 
