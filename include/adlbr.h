@@ -260,7 +260,8 @@ adlbr_status adlbr_unet_destroy(adlbr_unet *n);
  * tcgen05 implicit GEMMs with BF16 operands (activations and weights rounded
  * to BF16, accumulation in FP32; relative output differences to the FP32
  * forward of order 1e-2), weights repacked (one launch) at every forward
- * call.  For the inference path (the preconditioner): adlbr_unet_backward
+ * call; a preconditioned adlbr_step_implicit packs them once per solve, and
+ * the parameters must not change while it runs.  For the inference path (the preconditioner): adlbr_unet_backward
  * returns ADLBR_E_ARG after a tensor-core forward.  on = 0 returns to the FP32
  * kernels.  ADLBR_E_SHAPE if a layer has other than 16, 32 or 64 output
  * channels, or if its 9 packed weight taps and 4 staged input rows
