@@ -139,12 +139,52 @@ adlbr_status adlbr_stencils_destroy(adlbr_stencils *s);
  *  u    device, N elements of u_t (F64, F32, F16 or BF16).
  *  Au   device, N elements: double when u_t == ADLBR_F64, float otherwise
  *       (accumulation is in that type).  Must not alias u.
- * The transpose terms are added with atomic operations, so the rounding of
- * Au (and of the solvers built on it) can differ in the last bits from run to
- * run; the dot products and norms of the solvers reduce in a fixed order.
+ * In the scatter form the transpose terms are added with atomic operations,
+ * so the rounding of Au (and of the solvers built on it) can differ in the
+ * last bits from run to run; the gather form (adlbr_operator_form) is
+ * deterministic.  The dot products and norms of the solvers reduce in a
+ * fixed order.  The call that builds the handle's gather table synchronises
+ * the stream.
  */
 adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                          cudaStream_t stream);
+
+/*
+ * Form of the operator's evaluation (not in the paper, which applies an
+ * assembled sparse matrix).  Both forms compute the same A u (Eq. def:E*);
+ * they differ in the order of the FP32 additions only.
+ *
+ *  ADLBR_OP_SCATTER  one thread per point adds its own edges and pushes the
+ *                    transposed terms to the far ends (shared-memory and L2
+ *                    atomic additions); needs nothing but the stencils.
+ *  ADLBR_OP_GATHER   each point sums its whole row and writes it once: no
+ *                    atomics, so the results are the same bits from run to
+ *                    run.  It needs a table built from the stencils: per
+ *                    point its own weights, the weight its neighbour holds
+ *                    for each shared pair (the reciprocal offset), and a list
+ *                    of the remaining incoming edges, all at the point's F16
+ *                    scale (exact, except a neighbour weight below 2^-14 of
+ *                    the point's largest, which is rounded to the nearest F16
+ *                    subnormal there).  About 28 bytes per point plus 4 per
+ *                    incoming edge without a reciprocal, and 9 bytes per point
+ *                    of build temporaries; cudaMalloc on the first build, one
+ *                    stream synchronisation per build.  Available for 2D
+ *                    handles with F16 weights, vectors in F32, F16 or BF16,
+ *                    and offsets within +-127; elsewhere the scatter form
+ *                    runs.  Measured slower than the scatter form on GB300
+ *                    (2.0x on the 4096^2 CED stencils), so it is not the
+ *                    default.
+ *  ADLBR_OP_AUTO     (default) the scatter form.
+ * Rebuilding the stencils in place invalidates the table; it is rebuilt when
+ * next needed.
+ */
+typedef enum { ADLBR_OP_AUTO = 0, ADLBR_OP_SCATTER = 1, ADLBR_OP_GATHER = 2 } adlbr_operator_form;
+
+adlbr_status adlbr_stencils_set_operator(adlbr_stencils *s, int form);
+
+/* The handle's form setting, and 1 in *gather_ready when its gather table
+ * matches the current stencils (either pointer may be NULL). */
+adlbr_status adlbr_stencils_get_operator(const adlbr_stencils *s, int *form, int *gather_ready);
 
 /* Bytes of scratch that adlbr_step_explicit needs for u_t. */
 size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t);
@@ -155,7 +195,9 @@ size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t);
  *
  *  u        device, N elements of u_t; the result overwrites it.  For F16 and
  *           BF16 the update is computed in FP32 and rounded once per step.
- *  scratch  device, adlbr_step_scratch_bytes(s, u_t) bytes, caller-owned.
+ *  scratch  device, adlbr_step_scratch_bytes(s, u_t) bytes, caller-owned:
+ *           the accumulator of dt A u (scatter form), or the second buffer of
+ *           the u^n -> u^{n+1} ping-pong (gather form).
  *  dt       time step; the scheme is monotone for dt <= 1 / max_z A_zz.
  */
 adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch, adlbr_dtype u_t,

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libadlbr.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 NEUMANN, PERIODIC = 0, 1
+OP_AUTO, OP_SCATTER, OP_GATHER = 0, 1, 2
 
 STATUS = {0: "OK", 1: "E_ARG", 2: "E_SHAPE", 3: "E_NOT_SPD", 4: "E_NONFINITE",
           5: "E_NOT_CONVERGED", 6: "E_TIMEOUT", 7: "E_CUDA", 8: "E_RANGE", 9: "E_INTERNAL"}
@@ -61,6 +62,8 @@ def lib():
             "adlbr_stencils_export": (_i32, [_vp, _vp, _vp, _vp]),
             "adlbr_stencils_destroy": (_i32, [_vp]),
             "adlbr_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+            "adlbr_stencils_set_operator": (_i32, [_vp, _i32]),
+            "adlbr_stencils_get_operator": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
             "adlbr_step_scratch_bytes": (ctypes.c_size_t, [_vp, _i32]),
             "adlbr_step_explicit": (_i32, [_vp, _vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
             "adlbr_step_explicit_noalloc": (_i32, [_vp, _vp, _i32, ctypes.c_double, _i32, _vp]),
@@ -171,6 +174,18 @@ def adlbr_stencils_destroy(h):
 
 def adlbr_apply(h, u, Au, u_t, stream=None):
     _check(lib().adlbr_apply(h, _ptr(u), _ptr(Au), u_t, _stream(stream)))
+
+
+def adlbr_stencils_set_operator(h, form):
+    """form: OP_AUTO, OP_SCATTER or OP_GATHER."""
+    _check(lib().adlbr_stencils_set_operator(h, int(form)))
+
+
+def adlbr_stencils_get_operator(h):
+    """(form setting, 1 if the gather table matches the current stencils)."""
+    f, r = _i32(0), _i32(0)
+    _check(lib().adlbr_stencils_get_operator(h, ctypes.byref(f), ctypes.byref(r)))
+    return f.value, r.value
 
 
 def adlbr_step_scratch_bytes(h, u_t):

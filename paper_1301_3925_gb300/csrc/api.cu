@@ -48,7 +48,11 @@ static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_s
         bool same = s->dim == g->dim && s->w_t == w_t && s->n[0] == g->n[0] && s->n[1] == g->n[1] &&
                     (g->dim == 2 || s->n[2] == g->n[2]);
         if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type");
+        if (s->bc != g->bc) pull_free(s);
         s->bc = g->bc;
+        // the stencils are about to change: the gather table no longer matches
+        if (s->pull) s->pull->built = false;
+        s->applies_since_build = 0;
         return ADLBR_OK;
     }
     s = new (std::nothrow) adlbr_stencils();
@@ -144,6 +148,7 @@ adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
     if (s->err_host) cudaFreeHost(s->err_host);
     if (s->ws) cudaFree(s->ws);
     if (s->ws_nn) cudaFree(s->ws_nn);
+    pull_free(s);
     delete s;
     return ADLBR_OK;
 }
@@ -153,7 +158,24 @@ adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr
     if (adlbr_status st = check_handle(s)) return st;
     if (!u || !Au) return fail(ADLBR_E_ARG, "null vector");
     if (u == Au) return fail(ADLBR_E_ARG, "Au must not alias u");
-    return launch_apply(s, u, Au, u_t, stream);
+    if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
+    // the handle's gather table is a cache: building it does not change the operator
+    return launch_operator(const_cast<adlbr_stencils *>(s), u, u_t, Au, 0.0, 1.0, stream);
+}
+
+adlbr_status adlbr_stencils_set_operator(adlbr_stencils *s, int form) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (form != ADLBR_OP_AUTO && form != ADLBR_OP_SCATTER && form != ADLBR_OP_GATHER)
+        return fail(ADLBR_E_ARG, "unknown operator form %d", form);
+    s->op_form = form;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_stencils_get_operator(const adlbr_stencils *s, int *form, int *gather_ready) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (form) *form = s->op_form;
+    if (gather_ready) *gather_ready = pull_ready(s) ? 1 : 0;
+    return ADLBR_OK;
 }
 
 size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t) {
@@ -168,6 +190,25 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
     if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
     if (u_t < ADLBR_F64 || u_t > ADLBR_BF16) return fail(ADLBR_E_ARG, "bad u dtype");
     if (nsteps == 0) return ADLBR_OK;
+    adlbr_stencils *sm = const_cast<adlbr_stencils *>(s);   // gather table: a cache
+    bool gather = false;
+    if (u_t != ADLBR_F64)
+        if (adlbr_status st = choose_gather(sm, nsteps, &gather, stream)) return st;
+    if (gather) {
+        // u^{n+1} = u^n - dt A u^n written to the other buffer (u, scratch in turn)
+        void *src = u, *dst = scratch;
+        for (int k = 0; k < nsteps; ++k) {
+            if (adlbr_status st = launch_pull(s, src, u_t, dst, u_t, 1.0, -dt, nullptr, stream)) return st;
+            void *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != u) {
+            const size_t es = u_t == ADLBR_F32 ? 4 : 2;
+            ADLBR_CUDA(cudaMemcpyAsync(u, src, (size_t)s->N * es, cudaMemcpyDeviceToDevice, stream));
+        }
+        return ADLBR_OK;
+    }
     // per step: scratch <- 0, scratch += dt A u, u -= scratch
     for (int k = 0; k < nsteps; ++k) {
         ADLBR_CUDA(cudaMemsetAsync(scratch, 0, adlbr_step_scratch_bytes(s, u_t), stream));

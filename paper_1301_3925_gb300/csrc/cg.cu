@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
     }
 }
 
-// p <- z + beta p (z = r, or r / d) ; q <- p
-template <bool JAC>
+// p <- z + beta p (z = r, or r / d) ; q <- p (QP: for the scatter operator,
+// which accumulates dt A p into q; the gather operator writes q itself)
+template <bool JAC, bool QP>
 __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r, const float *__restrict__ inv_d,
                                             float *__restrict__ p, float *__restrict__ q, const CgState *S) {
     if (S->conv) return;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__
         const float zi = JAC ? r[i] * inv_d[i] : r[i];
         const float pi = zi + beta * p[i];
         p[i] = pi;
-        q[i] = pi;
+        if (QP) q[i] = pi;
     }
 }
 
@@ -249,6 +250,8 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
     CgWorkspace W;
     if (adlbr_status e = cg_workspace(s, W)) return e;
     const int64_t N = s->N;
+    bool gather = false;   // q = p + dt A p by the gather form of the operator
+    if (adlbr_status e = choose_gather(s, 2, &gather, st)) return e;
     if (jac)
         if (adlbr_status e = launch_jacobi_inverse(s, dt, W.inv_d, st)) return e;
     CgState init = {};
@@ -288,16 +291,22 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
         const int chunk = every > 0 ? every : 8;
         auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
             for (int k = 0; k < chunk; ++k) {
-                if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs))
+                if (gather) {
+                    if (adlbr_status e = launch_pull(s, W.p, ADLBR_F32, W.q, ADLBR_F32, 1.0, dt, conv_flag(W.S), cs))
+                        return e;
+                } else if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs)) {
                     return e;
+                }
                 cg_k2<<<RB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
                 if (jac) {
                     cg_k3<true><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
-                    cg_k4<true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    if (gather) cg_k4<true, false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    else cg_k4<true, true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
                 } else {
                     cg_k3<false><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2,
                                                     W.S);
-                    cg_k4<false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    if (gather) cg_k4<false, false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    else cg_k4<false, true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
                 }
             }
             ADLBR_CUDA(cudaGetLastError());

@@ -45,6 +45,26 @@ enum : int {
 // Lane types: F64 double, F32 float, F16 half (+ power-of-two scale).
 // meta: bit i (i < K) set when weight i is exactly zero; for F16 the high
 //       byte holds the signed exponent s of the per-point scale 2^s.
+namespace adlbr {
+// Table of the gather ("pull") form of a 2D operator (pull.cu).
+struct PullTable {
+    uint4 *recw = nullptr;      // per point: own and reciprocal weights (halves)
+    uint2 *reco = nullptr;      // per point: last reciprocal weight, scale, count, int8 offsets
+    uint32_t *ext = nullptr;    // extras (capacity cap + 4)
+    uint32_t *seg = nullptr;    // per 32-point row segment: first extra (nseg + 1)
+    int *cnt = nullptr;         // build temporaries
+    uint32_t *start = nullptr;
+    uint32_t *blk = nullptr;
+    uint8_t *pushm = nullptr;
+    int *flag = nullptr;        // device: the table does not fit its format
+    int *flag_host = nullptr;
+    int64_t nseg = 0, cap = 0;
+    int nseg_x = 0, nblk = 0;
+    bool built = false;         // matches the handle's current stencils
+    bool usable = false;        // built and within the format's ranges
+};
+}  // namespace adlbr
+
 struct adlbr_stencils {
     int dim;
     int bc;
@@ -61,6 +81,10 @@ struct adlbr_stencils {
     size_t ws_bytes;
     void *ws_nn;
     size_t ws_nn_bytes;
+    // operator form (adlbr_operator_form) and the gather table
+    int op_form;
+    int applies_since_build;
+    adlbr::PullTable *pull;
 };
 
 namespace adlbr {
@@ -318,6 +342,25 @@ struct ChunkGraph {
 };
 
 adlbr_status launch_finalize(const adlbr_stencils *s, void *u, void *acc, adlbr_dtype u_t,
+                             cudaStream_t st);
+
+// ---- gather (pull) form of the operator (pull.cu)
+bool pull_supported(const adlbr_stencils *s);
+// Builds the table for the handle's current stencils (synchronises st once).
+adlbr_status pull_build(adlbr_stencils *s, cudaStream_t st);
+void pull_free(adlbr_stencils *s);
+bool pull_ready(const adlbr_stencils *s);
+// out = a u + b A u by the gather form (requires pull_ready(s)); out is
+// F32, or u's own type for F16 / BF16 u.  Must not alias u.
+adlbr_status launch_pull(const adlbr_stencils *s, const void *u, adlbr_dtype u_t, void *out, adlbr_dtype out_t,
+                         double a, double b, const int *skip, cudaStream_t st);
+// Decides the form of the next operator applications on s: true = gather
+// (building the table first when needed).  `uses` is the number of
+// applications the caller is about to make with the current stencils.
+adlbr_status choose_gather(adlbr_stencils *s, int uses, bool *gather, cudaStream_t st);
+// out = a u + b A u by whichever form choose_gather picks (the scatter form
+// initialises out with a u, by a memset or a copy, and accumulates).
+adlbr_status launch_operator(adlbr_stencils *s, const void *u, adlbr_dtype u_t, void *out, double a, double b,
                              cudaStream_t st);
 
 }  // namespace adlbr

@@ -83,8 +83,9 @@ __device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z,
 // aligned (128-byte for TMA).  TMA: the u window (FP32, non-periodic grid,
 // nx % 4 == 0) arrives as one bulk tensor copy of the map's WW x WH box;
 // cells outside the grid are zero-filled, as the plain staging leaves them.
-// If the bounded wait for the copy gives up, the block records
-// ERRBIT_TIMEOUT in *err and returns.
+// One thread waits for the copy (bounded) while the others sleep in the block
+// barrier.  If the wait gives up, the block records ERRBIT_TIMEOUT in *err,
+// waits up to four more bounds for the copy to land, and returns.
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W, bool TMA = false>
 __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, const short4 *__restrict__ offs,
                                        const void *__restrict__ wbase, adlbr_dtype wt,
@@ -111,9 +112,17 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
         }
         for (int c4 = threadIdx.x; c4 < WH * WW / 4; c4 += NT)
             *reinterpret_cast<float4 *>(&aw[c4 * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool ok = tma::bar_wait(&bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0 && err) atomicOr(err, ERRBIT_TIMEOUT);
+        __shared__ int landed;
+        if (!tma::bar_wait_block(&bar, 0, &landed)) {
+            // the copy has not landed: record it, and wait longer before the
+            // block leaves, so that it does not exit while its window is
+            // still being written
+            if (threadIdx.x == 0) {
+                if (err) atomicOr(err, ERRBIT_TIMEOUT);
+                for (int t = 0; t < 4; ++t)
+                    if (tma::bar_wait(&bar, 0)) break;
+            }
+            __syncthreads();
             return;
         }
     } else {
@@ -293,9 +302,17 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
         }
         for (int c4 = threadIdx.x; c4 < B::CELLS / 4; c4 += NT)
             *reinterpret_cast<float4 *>(&aw[c4 * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool ok = tma::bar_wait(&bar, 0);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0 && err) atomicOr(err, ERRBIT_TIMEOUT);
+        __shared__ int landed;
+        if (!tma::bar_wait_block(&bar, 0, &landed)) {
+            // the copy has not landed: record it, and wait longer before the
+            // block leaves, so that it does not exit while its window is
+            // still being written
+            if (threadIdx.x == 0) {
+                if (err) atomicOr(err, ERRBIT_TIMEOUT);
+                for (int t = 0; t < 4; ++t)
+                    if (tma::bar_wait(&bar, 0)) break;
+            }
+            __syncthreads();
             return;
         }
     } else {

@@ -48,6 +48,18 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
+// Block-wide wait for the barrier's phase `parity`: one thread polls (bounded,
+// as bar_wait) while the others sleep in the block barrier, so that a waiting
+// block takes no issue slots from the blocks that compute beside it on the
+// SM.  Every thread of the block must call it; all get the same result.
+// The polling thread's acquire of the phase and the block barrier after it
+// make the copied data visible to every thread.
+__device__ __forceinline__ bool bar_wait_block(uint64_t *bar, unsigned parity, int *flag) {
+    if (threadIdx.x == 0) *flag = bar_wait(bar, parity) ? 1 : 0;
+    __syncthreads();
+    return *flag != 0;
+}
+
 // Box of the tensor map at element coordinates (x, y) into dst (16-byte
 // aligned); x * 4 bytes must be a multiple of 16 (FP32 maps: x % 4 == 0).
 // Cells outside the tensor are zero-filled.
