@@ -218,9 +218,11 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
  *  - Limit: at most 4,194,304 grid points for F32, F16 and BF16 u and
  *    2,097,152 for F64 u; larger grids return ADLBR_E_SHAPE.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.  Its
- *    first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it: make that first call before any
- *    stream capture.
+ *    first call on a device (nsteps may be 0 for this warm-up) looks up the
+ *    array's device address (cudaGetSymbolAddress) and caches it with the
+ *    current context: make that first call before any stream capture.  A
+ *    call under another context (for instance after cudaDeviceReset) looks
+ *    the address up again.
  *  - All calls share the one array, which keeps the last call's contents
  *    (each call clears the part it uses before using it).  Calls that may
  *    overlap on the GPU -- on different streams, for different handles or
@@ -264,6 +266,12 @@ adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, void *u, adlbr
  *  nn          preconditioner parameters (precond == 1), else ignored.
  *  iters_out   iterations performed (may be NULL).
  *  relres_out  final true relative residual |rhs - (I + dt A) x| / |rhs|.
+ * Every solver (precond 0, 1, 2) stops by the same rule: refinement rounds
+ * from the FP64 true residual, each run until the recursive residual meets
+ * rtol, while the true residual is above rtol and still halves per round.
+ * ADLBR_OK then means that the last round converged; the true residual may
+ * still sit above rtol at the FP32 floor of x (adlbr_last_residual_met()
+ * tells which).
  * The first call on a handle allocates its solver workspace (cudaMalloc);
  * later calls reuse it.  Synchronises the stream every few iterations.
  * Returns ADLBR_E_NOT_CONVERGED if maxit is reached first and
@@ -276,6 +284,12 @@ adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, do
 /* 1 if the last preconditioned adlbr_step_implicit call of this thread fell
  * back to plain CG, else 0 (thread-local; not in the paper). */
 int adlbr_last_fallback(void);
+
+/* 1 if the last adlbr_step_implicit call of this thread ended with its true
+ * relative residual (relres_out) at or below rtol, else 0 -- also when it
+ * returned ADLBR_OK at the FP32 floor of x above rtol, or failed
+ * (thread-local; not in the paper). */
+int adlbr_last_residual_met(void);
 
 /* ------------------------------------------------------------------------
  * Learned preconditioner network (not in the paper): a 3-level U-Net, FP32.

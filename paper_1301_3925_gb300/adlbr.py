@@ -71,6 +71,7 @@ def lib():
                                            _i32, _vp, ctypes.POINTER(_i32),
                                            ctypes.POINTER(ctypes.c_double), _vp]),
             "adlbr_last_fallback": (_i32, []),
+            "adlbr_last_residual_met": (_i32, []),
             "adlbr_unet_set_tensor_cores": (_i32, [_vp, _i32]),
             "adlbr_batch_create": (_i32, [_i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp), _vp]),
             "adlbr_batch_step": (_i32, [_vp, _i32, _vp]),
@@ -309,6 +310,11 @@ def adlbr_step_implicit(h, rhs, x, dt, rtol, maxit, precond=0, nn=None, stream=N
                                      int(precond), nnp, ctypes.byref(it), ctypes.byref(rr),
                                      _stream(stream)))
     return it.value, rr.value
+
+
+def adlbr_last_residual_met():
+    """1 if the last implicit solve of this thread ended at or below rtol (true residual)."""
+    return int(lib().adlbr_last_residual_met())
 
 
 def adlbr_last_fallback():

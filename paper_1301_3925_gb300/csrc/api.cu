@@ -10,6 +10,9 @@
 namespace adlbr {
 
 static thread_local char g_msg[512] = "";
+static thread_local int g_residual_met = 0;
+
+void set_last_residual_met(bool met) { g_residual_met = met ? 1 : 0; }
 
 adlbr_status fail(adlbr_status st, const char *fmt, ...) {
     va_list ap;
@@ -21,6 +24,18 @@ adlbr_status fail(adlbr_status st, const char *fmt, ...) {
 
 adlbr_status cuda_fail(cudaError_t e, const char *what) {
     return fail(ADLBR_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
 }
 
 adlbr_status check_handle(const adlbr_stencils *s) {
@@ -89,6 +104,8 @@ extern "C" {
 const char *adlbr_version(void) { return "adlbr-gb300 0.1 (sm_103a)"; }
 
 const char *adlbr_last_error(void) { return g_msg; }
+
+int adlbr_last_residual_met(void) { return g_residual_met; }
 
 adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
                                   adlbr_dtype w_t, adlbr_stencils **out, cudaStream_t stream) {
@@ -224,6 +241,7 @@ adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, do
     if (adlbr_status st = check_handle(s)) return st;
     if (!rhs || !x) return fail(ADLBR_E_ARG, "null vector");
     if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
+    set_last_residual_met(false);
     if (precond == 1)
         return run_fcg(s, (const float *)rhs, (float *)x, dt, rtol, maxit,
                        (const adlbr_nn_precond *)nn, iters_out, relres_out, stream);

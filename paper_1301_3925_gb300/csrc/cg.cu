@@ -31,7 +31,6 @@ namespace adlbr {
 
 namespace {
 
-constexpr int RB = 1216;  // blocks of the vector kernels (8 per SM on 152 SMs)
 
 struct CgState {
     double rr, rr_new, pq, alpha, beta, bb, tol2, rz;
@@ -185,7 +184,7 @@ struct CgWorkspace {
 };
 
 static size_t cg_ws_bytes(int64_t N) {
-    return 5 * (size_t)N * sizeof(float) + 4 * RB * sizeof(double) + 256 + sizeof(CgState);
+    return 5 * (size_t)N * sizeof(float) + 4 * vec_blocks() * sizeof(double) + 256 + sizeof(CgState);
 }
 
 static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
@@ -204,10 +203,10 @@ static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
     W.acc64 = (double *)W.q;
     W.inv_d = W.z + s->N;
     W.partials = (double *)(W.inv_d + s->N);
-    W.partials2 = W.partials + RB;
-    W.partials3 = W.partials2 + RB;
-    W.partials4 = W.partials3 + RB;
-    uintptr_t a = (uintptr_t)(W.partials4 + RB);
+    W.partials2 = W.partials + vec_blocks();
+    W.partials3 = W.partials2 + vec_blocks();
+    W.partials4 = W.partials3 + vec_blocks();
+    uintptr_t a = (uintptr_t)(W.partials4 + vec_blocks());
     a = (a + 255) & ~(uintptr_t)255;
     W.S = (CgState *)a;
     return ADLBR_OK;
@@ -267,10 +266,10 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
         ADLBR_CUDA(cudaMemsetAsync(W.acc64, 0, N * sizeof(double), st));
         if (adlbr_status e = launch_accumulate_f64(s, x, W.acc64, dt, st)) return e;
         if (jac)
-            cg_restart_kernel<true><<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
+            cg_restart_kernel<true><<<vec_blocks(), RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
                                                        W.partials2, W.partials3, W.partials4, W.S);
         else
-            cg_restart_kernel<false><<<RB, RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
+            cg_restart_kernel<false><<<vec_blocks(), RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
                                                         W.partials2, W.partials3, W.partials4, W.S);
         ADLBR_CUDA(cudaGetLastError());
         // q = p (q aliases acc64, which the restart kernel has consumed)
@@ -297,16 +296,16 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
                 } else if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs)) {
                     return e;
                 }
-                cg_k2<<<RB, RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
+                cg_k2<<<vec_blocks(), RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
                 if (jac) {
-                    cg_k3<true><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
-                    if (gather) cg_k4<true, false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                    else cg_k4<true, true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    cg_k3<true><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
+                    if (gather) cg_k4<true, false><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    else cg_k4<true, true><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
                 } else {
-                    cg_k3<false><<<RB, RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2,
+                    cg_k3<false><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2,
                                                     W.S);
-                    if (gather) cg_k4<false, false><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                    else cg_k4<false, true><<<RB, RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    if (gather) cg_k4<false, false><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+                    else cg_k4<false, true><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
                 }
             }
             ADLBR_CUDA(cudaGetLastError());
@@ -341,6 +340,7 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
     }
     if (iters_out) *iters_out = total_iters;
     if (relres_out) *relres_out = relres;
+    set_last_residual_met(relres <= rtol);
     if (!(relres <= rtol) && !cg_converged)
         return fail(ADLBR_E_NOT_CONVERGED, "CG stopped at relative residual %.3e after %d iterations",
                     relres, total_iters);

@@ -220,6 +220,11 @@ __device__ __forceinline__ unsigned load_weights(const void *wbase, adlbr_dtype 
 }
 
 // ---------------------------------------------------------------- launch helpers
+// Number of SMs of the current device (queried once per device).
+int sm_count();
+// Blocks of the grid-stride vector and reduction kernels: 8 per SM.
+inline int vec_blocks() { return 8 * sm_count(); }
+
 inline unsigned blocks_for(int64_t n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
@@ -298,6 +303,9 @@ typedef adlbr_status (*CgHook)(void *ctx, const float *r, const float *x, int it
 adlbr_status run_cg_hooked(adlbr_stencils *s, const float *b, float *x, double dt, double rtol,
                            int maxit, int *iters_out, double *relres_out, int every, CgHook hook,
                            void *ctx, cudaStream_t st);
+// Records whether the last implicit solve of the calling thread ended with
+// its true relative residual at or below rtol (adlbr_last_residual_met).
+void set_last_residual_met(bool met);
 // CG preconditioned by the diagonal 1 + dt A_zz (same stopping test as run_cg)
 adlbr_status run_pcg_jacobi(adlbr_stencils *s, const float *b, float *x, double dt, double rtol, int maxit,
                             int *iters_out, double *relres_out, cudaStream_t st);

@@ -28,7 +28,6 @@ constexpr int RF = 4;                 // restriction factor
 constexpr int NR = RF * RF;           // residual channels (space to depth)
 constexpr int NS = 9;                 // static channels (stencil block means)
 constexpr int NF = NR + NS;           // network input channels
-constexpr int NB = 1216;     // blocks of the vector kernels
 
 struct FcgState {
     double rr, bb, tol2, rz, pq, alpha, beta, s, gamma;
@@ -235,16 +234,16 @@ __global__ void static_nhwc_kernel(int64_t Nc, int cp, const float *__restrict__
     }
 }
 
-// r = b - (x + q) (q = dt A x), rr, bb.  As in the CG kernels, no kernel
-// here stores a constant over a value it has just loaded; q receives p in
-// the kernels that produce p, and the operator accumulates dt A p into it.
-__global__ void __launch_bounds__(RT) fcg_init_kernel(int64_t N, const float *__restrict__ b,
-                                                      const float *__restrict__ x, const float *__restrict__ q,
-                                                      float *__restrict__ r, double *partials,
-                                                      double *partials2, FcgState *S) {
+// (Re)start of a refinement round: r = b - (x + dt A x) with dt A x
+// accumulated in FP64 (acc), rounded once to FP32; |r|^2 of the FP32 copy and
+// |b|^2; conv = 1 when it already meets the tolerance.
+__global__ void __launch_bounds__(RT) fcg_init64_kernel(int64_t N, const float *__restrict__ b,
+                                                        const float *__restrict__ x, const double *__restrict__ acc,
+                                                        float *__restrict__ r, double *partials,
+                                                        double *partials2, FcgState *S) {
     FFAcc s_rr, s_bb;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        const float ri = b[i] - (x[i] + q[i]);
+        const float ri = (float)((double)b[i] - ((double)x[i] + acc[i]));
         r[i] = ri;
         ff_add_prod(s_rr, ri, ri);
         ff_add_prod(s_bb, b[i], b[i]);
@@ -480,7 +479,7 @@ struct NnWorkspace {
 
 static adlbr_status nn_workspace(adlbr_stencils *s, NnWorkspace &W) {
     const int64_t N = s->N, Nc = N / (RF * RF);
-    size_t need = (10 * (size_t)N + (NF + 1) * (size_t)Nc) * sizeof(float) + 3 * NB * sizeof(double) + 4096;
+    size_t need = (10 * (size_t)N + (NF + 1) * (size_t)Nc) * sizeof(float) + 3 * vec_blocks() * sizeof(double) + 4096;
     if (!s->ws_nn || s->ws_nn_bytes < need) {
         if (s->ws_nn) cudaFree(s->ws_nn);
         s->ws_nn = nullptr;
@@ -503,8 +502,8 @@ static adlbr_status nn_workspace(adlbr_stencils *s, NnWorkspace &W) {
     uintptr_t a = (uintptr_t)(W.y + Nc);
     a = (a + 255) & ~(uintptr_t)255;
     W.partials = (double *)a;
-    W.partials2 = W.partials + NB;
-    W.scal = W.partials2 + NB;
+    W.partials2 = W.partials + vec_blocks();
+    W.scal = W.partials2 + vec_blocks();
     a = (uintptr_t)(W.scal + 4);
     a = (a + 255) & ~(uintptr_t)255;
     W.S = (FcgState *)a;
@@ -516,7 +515,7 @@ static adlbr_status nn_workspace(adlbr_stencils *s, NnWorkspace &W) {
     a = (uintptr_t)(W.Sh + 1);
     a = (a + 255) & ~(uintptr_t)255;
     W.partials_h = (double *)a;
-    W.scal_h = W.partials_h + NB;
+    W.scal_h = W.partials_h + vec_blocks();
     W.cnt_h = (unsigned *)(W.scal_h + 2);
     return ADLBR_OK;
 }
@@ -596,7 +595,7 @@ static adlbr_status precondition(adlbr_stencils *s, NnWorkspace &W, adlbr_unet *
     dim3 gc(blocks_for(nx / RF, 128), (unsigned)(ny / RF));
     coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, s->N, W.feat);
     if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
-    fcg_z_kernel<FIRST><<<NB, RT, 0, st>>>(nx, s->N, W.r, W.r_old, W.d, W.y, W.z, W.p, W.q,
+    fcg_z_kernel<FIRST><<<vec_blocks(), RT, 0, st>>>(nx, s->N, W.r, W.r_old, W.d, W.y, W.z, W.p, W.q,
                                            W.partials, W.partials2, W.S);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
@@ -632,13 +631,13 @@ static adlbr_status galerkin_direction(adlbr_stencils *s, NnWorkspace &W, adlbr_
         coarse_r_kernel<<<gc, 128, 0, st>>>(nx, ny, W.r, W.S, N, W.feat);
         if (adlbr_status e = unet_forward(net, params, W.feat, W.y, st)) return e;
     }
-    fcg_w_kernel<<<NB, RT, 0, st>>>(nx, N, W.r, W.d, W.y, W.z, W.c, W.g1, W.g2, W.S);
+    fcg_w_kernel<<<vec_blocks(), RT, 0, st>>>(nx, N, W.r, W.d, W.y, W.z, W.c, W.g1, W.g2, W.S);
     if (adlbr_status e = launch_accumulate(s, W.z, W.g1, ADLBR_F32, dt, skip, st)) return e;
     if (adlbr_status e = launch_accumulate(s, W.c, W.g2, ADLBR_F32, dt, skip, st)) return e;
-    fcg_gamma_kernel<<<NB, RT, 0, st>>>(N, W.r, W.c, W.g1, W.g2, W.partials, W.partials2, W.S);
-    fcg_z2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.r, W.r_old, W.z, W.c, W.g1, W.g2, W.partials, W.partials2,
+    fcg_gamma_kernel<<<vec_blocks(), RT, 0, st>>>(N, W.r, W.c, W.g1, W.g2, W.partials, W.partials2, W.S);
+    fcg_z2_kernel<FIRST><<<vec_blocks(), RT, 0, st>>>(N, W.r, W.r_old, W.z, W.c, W.g1, W.g2, W.partials, W.partials2,
                                             W.S);
-    fcg_p2_kernel<FIRST><<<NB, RT, 0, st>>>(N, W.z, W.g1, W.p, W.q, W.partials, W.S);
+    fcg_p2_kernel<FIRST><<<vec_blocks(), RT, 0, st>>>(N, W.z, W.g1, W.p, W.q, W.partials, W.S);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
 }
@@ -664,24 +663,18 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
         int cp = 0;
         if (__nv_bfloat16 *xh = unet_tc_input(nn->net, &cp)) {
             const int64_t Nc = N / (RF * RF);
-            static_nhwc_kernel<<<(unsigned)std::min<int64_t>((Nc + 255) / 256, 152 * 8), 256, 0, st>>>(Nc, cp, W.feat,
+            static_nhwc_kernel<<<(unsigned)std::min<int64_t>((Nc + 255) / 256, vec_blocks()), 256, 0, st>>>(Nc, cp, W.feat,
                                                                                                      xh);
             if (adlbr_status e = unet_tc_prepare(nn->net, nn->params, st)) return e;
         }
     }
     FcgState init = {};
     init.tol2 = rtol * rtol;
-    init.max_iters = maxit;
-    ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(FcgState), cudaMemcpyHostToDevice, st));
-    ADLBR_CUDA(cudaMemsetAsync(W.q, 0, N * sizeof(float), st));
-    if (adlbr_status e = launch_accumulate(s, x, W.q, ADLBR_F32, dt, nullptr, st)) return e;
-    fcg_init_kernel<<<NB, RT, 0, st>>>(N, b, x, W.q, W.r, W.partials, W.partials2, W.S);
-    ADLBR_CUDA(cudaGetLastError());
     const int *skip = (const int *)((const char *)W.S + offsetof(FcgState, conv));
-    if (adlbr_status e = galerkin_direction<true>(s, W, nn->net, nn->params, dt, skip, st)) return e;
+    // q and z hold 8N bytes: the FP64 accumulator of dt A x between rounds
+    double *acc64 = (double *)W.q;
     FcgState host = {};
     const int chunk = every > 0 ? every : 2;
-    int it = 0;
     // Plain CG is the fallback of a user solve: the initial guess is kept, and
     // when the recursive residual of the preconditioned solve grows tenfold
     // above its best value, or fails to halve within kStall iterations, the
@@ -691,78 +684,107 @@ static adlbr_status run_fcg_hooked(adlbr_stencils *s, const float *b, float *x, 
         g_fallback = 0;
         ADLBR_CUDA(cudaMemcpyAsync(W.xs, x, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
-    double best = INFINITY;
-    int best_it = 0;
-    bool fall_back = false;
     auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
         for (int k = 0; k < chunk; ++k) {
             // q = (I + dt A) p is carried by the recurrences (no operator
             // here) and alpha was set with p and q
-            fcg_x_kernel<<<NB, RT, 0, cs>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
+            fcg_x_kernel<<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.r_old, W.q, W.partials, W.S);
             if (adlbr_status e = galerkin_direction<false>(s, W, nn->net, nn->params, dt, skip, cs)) return e;
         }
         ADLBR_CUDA(cudaGetLastError());
         return ADLBR_OK;
     };
     // the chunk (about 25 launches per iteration, most of them the network's)
-    // is recorded once per solve and replayed; the first direction above ran
-    // uncaptured, so the kernels' one-time attribute settings are done
+    // is recorded once per solve, after the first direction ran uncaptured
+    // (so the kernels' one-time attribute settings are done), and replayed
     ChunkGraph graph;
-    if (!hook)
-        if (adlbr_status e = graph.capture(enqueue_chunk)) return e;
-    while (it < maxit) {
-        if (hook)
-            if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
-        if (graph.exec) {
-            ADLBR_CUDA(cudaGraphLaunch(graph.exec, st));
-        } else if (adlbr_status e = enqueue_chunk(st)) {
-            return e;
-        }
-        it += chunk;
+    // Refinement rounds, as in plain CG: every round starts from the true
+    // residual b - (I + dt A) x evaluated in FP64 and runs the flexible
+    // iteration until the recursive residual meets rtol; a new round follows
+    // while the true residual is above rtol and still halves per round.
+    const int kMaxRestarts = 3;
+    int total_iters = 0;
+    double relres = INFINITY, prev = INFINITY;
+    bool converged = false, fall_back = false;
+    for (int round = 0; round <= kMaxRestarts; ++round) {
+        init.max_iters = maxit - total_iters;
+        ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(FcgState), cudaMemcpyHostToDevice, st));
+        ADLBR_CUDA(cudaMemsetAsync(acc64, 0, N * sizeof(double), st));
+        if (adlbr_status e = launch_accumulate_f64(s, x, acc64, dt, st)) return e;
+        fcg_init64_kernel<<<vec_blocks(), RT, 0, st>>>(N, b, x, acc64, W.r, W.partials, W.partials2, W.S);
+        ADLBR_CUDA(cudaGetLastError());
         ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
         ADLBR_CUDA(cudaStreamSynchronize(st));
-        if (host.conv == 3 && !hook) {   // non-finite: the preconditioner failed
-            fall_back = true;
-            break;
-        }
-        if (host.conv) break;
-        if (!hook) {
-            const double rel = host.bb > 0 ? std::sqrt(host.rr / host.bb) : 0.0;
-            if (rel < 0.5 * best) best = rel, best_it = it;
-            if (!(rel <= 10.0 * best) || it - best_it >= kStall) {
+        if (!std::isfinite(host.bb) || !std::isfinite(host.rr))
+            return fail(ADLBR_E_NONFINITE, "non-finite right-hand side or iterate in the preconditioned solve");
+        // the FP32 residual's norm stands for the true one at the round start
+        relres = host.bb > 0 ? std::sqrt(host.rr / host.bb) : 0.0;
+        if (relres <= rtol || total_iters >= maxit || round == kMaxRestarts) break;
+        if (round > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
+        prev = relres;
+        if (adlbr_status e = galerkin_direction<true>(s, W, nn->net, nn->params, dt, skip, st)) return e;
+        if (!hook && !graph.exec)
+            if (adlbr_status e = graph.capture(enqueue_chunk)) return e;
+        double best = INFINITY;
+        int best_it = 0, it = 0;
+        while (it < maxit - total_iters) {
+            if (hook && round == 0)
+                if (adlbr_status e = hook(ctx, W.r, x, it, st)) return e;
+            if (graph.exec) {
+                ADLBR_CUDA(cudaGraphLaunch(graph.exec, st));
+            } else if (adlbr_status e = enqueue_chunk(st)) {
+                return e;
+            }
+            it += chunk;
+            ADLBR_CUDA(cudaMemcpyAsync(&host, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
+            ADLBR_CUDA(cudaStreamSynchronize(st));
+            if (host.conv == 3 && !hook) {   // non-finite: the preconditioner failed
                 fall_back = true;
                 break;
             }
+            if (host.conv) break;
+            if (!hook) {
+                const double rel = host.bb > 0 ? std::sqrt(host.rr / host.bb) : 0.0;
+                if (rel < 0.5 * best) best = rel, best_it = it;
+                if (!(rel <= 10.0 * best) || it - best_it >= kStall) {
+                    fall_back = true;
+                    break;
+                }
+            }
         }
+        total_iters += host.iters;
+        if (fall_back) break;
+        converged = host.conv == 1;
+        if (host.conv == 3)
+            return fail(ADLBR_E_NONFINITE, "preconditioned CG residual became non-finite after %d iterations",
+                        total_iters);
+        if (!converged) break;   // iteration limit
     }
     if (fall_back) {
         g_fallback = 1;
         ADLBR_CUDA(cudaMemcpyAsync(x, W.xs, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         int cg_it = 0;
-        const adlbr_status e = run_cg(s, b, x, dt, rtol, std::max(1, maxit - it), &cg_it, relres_out, st);
-        if (iters_out) *iters_out = it + cg_it;
+        const adlbr_status e = run_cg(s, b, x, dt, rtol, std::max(1, maxit - total_iters), &cg_it, relres_out, st);
+        if (iters_out) *iters_out = total_iters + cg_it;
         return e;
     }
-    // true residual with the operator accumulated in FP64 (q and z hold 8N bytes)
-    double *acc64 = (double *)W.q;
+    // the final true residual, FP64 throughout
     ADLBR_CUDA(cudaMemsetAsync(acc64, 0, N * sizeof(double), st));
     if (adlbr_status e = launch_accumulate_f64(s, x, acc64, dt, st)) return e;
     ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(FcgState), cudaMemcpyHostToDevice, st));
-    resid64_kernel<<<NB, RT, 0, st>>>(N, b, x, acc64, W.partials, W.partials2, W.S);
+    resid64_kernel<<<vec_blocks(), RT, 0, st>>>(N, b, x, acc64, W.partials, W.partials2, W.S);
     FcgState fin = {};
     ADLBR_CUDA(cudaMemcpyAsync(&fin, W.S, sizeof(FcgState), cudaMemcpyDeviceToHost, st));
     ADLBR_CUDA(cudaStreamSynchronize(st));
     if (!std::isfinite(fin.bb) || !std::isfinite(fin.rr))
         return fail(ADLBR_E_NONFINITE, "non-finite right-hand side or iterate in the preconditioned solve");
-    const double relres = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
-    if (iters_out) *iters_out = host.iters;
+    relres = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
+    if (iters_out) *iters_out = total_iters;
     if (relres_out) *relres_out = relres;
-    if (host.conv == 3)
-        return fail(ADLBR_E_NONFINITE, "preconditioned CG residual became non-finite after %d iterations",
-                    host.iters);
-    if (host.conv != 1)
+    set_last_residual_met(relres <= rtol);
+    if (!(relres <= rtol) && !converged)
         return fail(ADLBR_E_NOT_CONVERGED, "preconditioned CG stopped after %d iterations (residual %.3e)",
-                    host.iters, relres);
+                    total_iters, relres);
     return ADLBR_OK;
 }
 
@@ -786,7 +808,7 @@ adlbr_status pair_hook(void *vctx, const float *r, const float *x, int iter, cud
     const int64_t Nc = s->N / (RF * RF);
     // the hook runs inside a solve: it uses its own state and partials
     ADLBR_CUDA(cudaMemsetAsync(W.cnt_h, 0, sizeof(unsigned), st));
-    sumsq_kernel<<<NB, RT, 0, st>>>(s->N, r, W.partials_h, W.cnt_h, W.scal_h);
+    sumsq_kernel<<<vec_blocks(), RT, 0, st>>>(s->N, r, W.partials_h, W.cnt_h, W.scal_h);
     double ss = 0.0;
     ADLBR_CUDA(cudaMemcpyAsync(&ss, W.scal_h, sizeof(double), cudaMemcpyDeviceToHost, st));
     ADLBR_CUDA(cudaStreamSynchronize(st));
@@ -852,7 +874,7 @@ adlbr_status nn_apply(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt, 
     static_features(s, W, dt, st);
     ADLBR_CUDA(cudaMemcpyAsync(W.r, r, s->N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     ADLBR_CUDA(cudaMemsetAsync(W.cnt, 0, sizeof(unsigned), st));
-    sumsq_kernel<<<NB, RT, 0, st>>>(s->N, r, W.partials, W.cnt, W.scal);
+    sumsq_kernel<<<vec_blocks(), RT, 0, st>>>(s->N, r, W.partials, W.cnt, W.scal);
     double ss = 0.0;
     ADLBR_CUDA(cudaMemcpyAsync(&ss, W.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     ADLBR_CUDA(cudaStreamSynchronize(st));
@@ -899,13 +921,13 @@ adlbr_status mse_grad(const float *y, const float *t, int64_t n, float *gy, doub
     int dev = -1;
     ADLBR_CUDA(cudaGetDevice(&dev));
     if (!buf || dev != dev_of_buf) {
-        ADLBR_CUDA(cudaMalloc(&buf, (NB + 64) * sizeof(double)));
-        ADLBR_CUDA(cudaMemset(buf, 0, (NB + 64) * sizeof(double)));
+        ADLBR_CUDA(cudaMalloc(&buf, (vec_blocks() + 64) * sizeof(double)));
+        ADLBR_CUDA(cudaMemset(buf, 0, (vec_blocks() + 64) * sizeof(double)));
         dev_of_buf = dev;
     }
-    unsigned *count = (unsigned *)(buf + NB);
-    double *out = buf + NB + 8;
-    mse_kernel<<<NB, RT, 0, st>>>(n, y, t, gy, buf, count, out);
+    unsigned *count = (unsigned *)(buf + vec_blocks());
+    double *out = buf + vec_blocks() + 8;
+    mse_kernel<<<vec_blocks(), RT, 0, st>>>(n, y, t, gy, buf, count, out);
     ADLBR_CUDA(cudaGetLastError());
     if (loss) {
         ADLBR_CUDA(cudaMemcpyAsync(loss, out, sizeof(double), cudaMemcpyDeviceToHost, st));

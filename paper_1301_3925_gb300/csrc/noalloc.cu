@@ -1,6 +1,9 @@
 // adlbr_step_explicit_noalloc: the explicit step with its scratch buffer in a
 // fixed device array of this library instead of caller- or library-allocated
 // memory (see include/adlbr.h for who needs it and its limits).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -17,20 +20,47 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
+struct Cached {
+    CUcontext ctx = nullptr;   // the context the address belongs to
+    void *addr = nullptr;
+};
+Cached g_cache[kMaxDevices];
 
-// Device address of g_noalloc_scratch on the current device (looked up once
-// per device; the host-side name is only a stand-in, never a device address).
+// The calling thread's current context (driver entry point looked up once);
+// nullptr if the driver entry point is unavailable.
+CUcontext current_context() {
+    static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    });
+    CUcontext c = nullptr;
+    if (get) get(&c);
+    return c;
+}
+
+// Device address of g_noalloc_scratch on the current device (the host-side
+// name is only a stand-in, never a device address).  Looked up with the
+// device current and cached per device together with the context it was
+// taken in; a different current context (after a device reset, say) makes
+// the next call look it up again.
 adlbr_status scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(ADLBR_E_ARG, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    const CUcontext ctx = current_context();
+    Cached &c = g_cache[dev];
+    if (!c.addr || c.ctx != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_addr[dev] = p;
+        c.addr = p;
+        c.ctx = current_context();   // the lookup may have made the primary context current
     }
-    *out = g_addr[dev];
+    *out = c.addr;
     return ADLBR_OK;
 }
 
@@ -61,9 +91,11 @@ extern "C" adlbr_status adlbr_step_explicit_noalloc(const adlbr_stencils *s, voi
     ADLBR_CUDA(cudaGetDevice(&dev));
     if (dev != s->device)
         return fail(ADLBR_E_ARG, "current device %d is not the handle's device %d", dev, s->device);
-    if (nsteps == 0) return ADLBR_OK;
+    // the set-up (the array's address on this device) happens on every
+    // device's first call, also one with nsteps == 0
     void *acc = nullptr;
     if (adlbr_status st = scratch_address(dev, &acc)) return st;
+    if (nsteps == 0) return ADLBR_OK;
     // per step: clear the accumulator, accumulate dt A u, subtract it
     const size_t bytes = (size_t)s->N * (u_t == ADLBR_F64 ? sizeof(double) : sizeof(float));
     for (int k = 0; k < nsteps; ++k) {

@@ -327,7 +327,7 @@ adlbr_status launch_tc(int B, int H, int W, const ConvMaps &maps, int g0, int kp
     // their copies.
     const int cols = (W + TCM - 1) / TCM;
     const int64_t tiles = (int64_t)cols * H * B;
-    int rows = (int)std::max<int64_t>(1, (tiles + 8 * 152 - 1) / (8 * 152));
+    int rows = (int)std::max<int64_t>(1, (tiles + vec_blocks() - 1) / vec_blocks());
     rows = std::min(rows, H);
     dim3 grid(cols, (H + rows - 1) / rows, B);
     conv3x3_tc_kernel<CO><<<grid, NT_TC, smem, st>>>(maps, g0, kp, nslot, H, W, rows, wpack, bias, y);
@@ -435,7 +435,7 @@ __global__ void out1x1_nhwc_kernel(int64_t n, int C, const __nv_bfloat16 *__rest
     }
 }
 
-unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * vec_blocks())); }
 
 }  // namespace
 

@@ -153,3 +153,48 @@ def test_fused_tensor_full_size_samples():
         win = useen[y - 32:y + 32, x - 32:x + 32]
         Do = np.stack(ced.ced_tensor(win, P["sigma"], P["rho"], P["alpha"], P["C"]))
         assert np.abs(Df[:, y, x] - Do[:, 32, 32]).max() <= 2e-5
+
+
+def test_ced_stencils_bitexact_on_gpu_tensor_4096():
+    """The benchmark's 4096^2 CED step: the GPU's own tensor D(u) is fed to
+    the oracle's construction (Sec. 2), at 200,000 sampled points and at every
+    point where D is exactly alpha I (the degenerate tensors of flat regions):
+    offsets bit-exact, F16 weights within their storage precision.  The fused
+    tensor + stencil kernel (adlbr_ced_stencils) gives the same stencils."""
+    from gpu_helpers import weight_tol
+    t = torch()
+    n = 4096
+    N = n * n
+    g = ab.grid((n, n))
+    u = t.from_numpy(synth.fingerprint(n, 1).astype(np.float32).ravel()).cuda()
+    scratch = t.empty(ab.adlbr_ced_scratch_bytes(g), dtype=t.uint8, device="cuda")
+    D = t.empty(3 * N, dtype=t.float32, device="cuda")
+    ab.adlbr_ced_tensor(g, u, D, P["sigma"], P["rho"], P["alpha"], P["C"], scratch)
+    h = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+    hf = ab.adlbr_ced_stencils(None, g, u, scratch, P["sigma"], P["rho"], P["alpha"], P["C"], ab.F16)
+    try:
+        ab.adlbr_stencils_check(h)
+        ab.adlbr_stencils_check(hf)
+        Dp = D.view(3, N)
+        iso = ((Dp[1] == 0) & (Dp[0] == Dp[2])).nonzero().flatten()
+        rng = np.random.default_rng(3)
+        samp = t.from_numpy(rng.choice(N, 200000, replace=False)).cuda()
+        idx = t.unique(t.cat([samp, iso]))
+        outs = []
+        for hh in (h, hf):
+            offs = t.zeros((N, 3, 2), dtype=t.int16, device="cuda")
+            w = t.zeros((N, 3), dtype=t.float32, device="cuda")
+            ab.adlbr_stencils_export(hh, offs, w)
+            outs.append((offs[idx].cpu().numpy().astype(np.int32), w[idx].double().cpu().numpy()))
+            del offs, w
+        Ds = Dp[:, idx].double().cpu().numpy()
+    finally:
+        ab.adlbr_stencils_destroy(h)
+        ab.adlbr_stencils_destroy(hf)
+    assert iso.numel() > 0, "no exactly isotropic tensor in the workload"
+    oo, ow, st, _ = oracle.build2d(Ds[0], Ds[1], Ds[2])
+    assert np.all(st == 0)
+    go, gw = outs[0]
+    assert np.array_equal(go, oo), np.argwhere(np.any(go != oo, axis=(1, 2)))[:5]
+    assert np.all(np.abs(gw - ow) <= weight_tol(ow, ab.F16, np.abs(Ds).max()))
+    assert np.array_equal(outs[1][0], go) and np.array_equal(outs[1][1], gw)

@@ -162,3 +162,30 @@ def test_jacobi_pcg_matches_cg_with_fewer_iterations(shape):
     assert rel_j <= 2e-5 and rel_cg <= 2e-5, (rel_j, rel_cg)
     assert d <= 5e-5, d
     assert it_j < it_cg, (it_j, it_cg)
+
+
+def test_residual_met_flag():
+    """adlbr_last_residual_met: 1 when the true residual of the returned x is
+    at or below rtol; 0 when rtol lies below the FP32 floor of x (the solve
+    still returns OK once its last refinement round converged)."""
+    t = torch()
+    shape = (64, 80)
+    D = synth.smooth_field2d(*shape, seed=3, kappa_min=1, kappa_max=20, lattice=8)
+    h, seen, _ = build(D, shape, t.float32, ab.F32)
+    oo, ow, st, _ = oracle.build2d(*seen.reshape(3, -1))
+    try:
+        bd = dev(synth.u_uniform(shape, 3).ravel(), t.float32)
+        dt = 2.0 * oracle.dt_limit(shape, ab.NEUMANN, oo, ow)
+        for precond in (0, 2):
+            x = bd.clone()
+            _, rel = ab.adlbr_step_implicit(h, bd, x, dt, 1e-5, 2000, precond=precond)
+            assert rel <= 1e-5 and ab.adlbr_last_residual_met() == 1
+            x = bd.clone()
+            try:
+                _, rel = ab.adlbr_step_implicit(h, bd, x, 200.0 * dt, 1e-9, 4000, precond=precond)
+                assert rel > 1e-9, rel
+            except ab.AdlbrError as e:   # the recursive residual may not reach 1e-9 either
+                assert e.status == 5, e
+            assert ab.adlbr_last_residual_met() == 0
+    finally:
+        ab.adlbr_stencils_destroy(h)

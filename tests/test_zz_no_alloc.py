@@ -21,13 +21,18 @@ from gpu_helpers import build, dev, torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("u_name,w_t", [("float32", ab.F32), ("float64", ab.F64)])
-def test_noalloc_step_matches_step_explicit(u_name, w_t):
+@pytest.mark.parametrize("u_name,w_t,dim", [("float32", ab.F32, 2), ("float64", ab.F64, 2),
+                                             ("bfloat16", ab.F16, 2), ("float32", ab.F16, 3)])
+def test_noalloc_step_matches_step_explicit(u_name, w_t, dim):
     t = torch()
-    shape = (181, 233)
-    D = synth.smooth_field2d(*shape, seed=11, kappa_min=1, kappa_max=60, lattice=8)
+    if dim == 2:
+        shape = (181, 233)
+        D = synth.smooth_field2d(*shape, seed=11, kappa_min=1, kappa_max=60, lattice=8)
+    else:
+        shape = (21, 26, 31)
+        D = synth.needle_field3d(31, seed=4, kappa=15.0)[:, :21, :26, :31]
     ud = getattr(t, u_name)
-    h, seen, _ = build(D, shape, t.float32 if ud == t.float32 else t.float64, w_t)
+    h, seen, _ = build(D, shape, t.float64 if ud == t.float64 else t.float32, w_t)
     try:
         ab.adlbr_stencils_check(h)
         code = ab.dtype_code(ud)
@@ -39,14 +44,26 @@ def test_noalloc_step_matches_step_explicit(u_name, w_t):
         # the fixed array is shared by every call and keeps old contents:
         # two calls in a row must each match the reference
         got = u0.clone()
+        ab.adlbr_step_explicit_noalloc(h, got, code, dt, 0)   # set-up call: no step
+        t.cuda.synchronize()
+        assert t.equal(got, u0)
         for nsteps in (3, 2):
             ab.adlbr_step_explicit(h, ref, scratch, code, dt, nsteps)
+            t.cuda.synchronize()
+            # the call itself allocates nothing: device memory in use and the
+            # torch allocator's statistics are the same before and after
+            free0, _ = t.cuda.mem_get_info()
+            alloc0 = t.cuda.memory_allocated()
             ab.adlbr_step_explicit_noalloc(h, got, code, dt, nsteps)
             t.cuda.synchronize()
+            assert t.cuda.mem_get_info()[0] == free0
+            assert t.cuda.memory_allocated() == alloc0
             r = ref.double().cpu().numpy()
             g = got.double().cpu().numpy()
             # same kernels; only the order of the FP atomic additions differs
-            tol = 1e-6 if ud == t.float32 else 1e-13
+            # (BF16: each step rounds u once, so a last-bit difference of an
+            # intermediate step can move the result by one BF16 ulp)
+            tol = {t.float32: 1e-6, t.float64: 1e-13, t.bfloat16: 2 ** -7}[ud]
             assert np.abs(g - r).max() <= tol * np.abs(r).max()
     finally:
         ab.adlbr_stencils_destroy(h)
