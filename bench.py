@@ -78,6 +78,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-step measurement")
     p.add_argument("--no-ced3d", action="store_true", help="skip the 3D CED measurement")
     p.add_argument("--no-spectral", action="store_true", help="skip the periodic spectral study")
+    p.add_argument("--no-ann", action="store_true", help="skip the A-NN comparison scheme")
     p.add_argument("--precision-steps", type=int, default=100)
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
@@ -481,6 +482,52 @@ def spectral_measurement(n=128, k=7):
     return {"grid": [n, n], "D": D.tolist(), "k": k, "lobpcg_iters": its, "ms": ms,
             "n2_lambda": [float(v) for v in scaled], "continuous": [float(v) for v in cont],
             "max_rel_dev": float(np.abs(scaled - cont)[1:].max() / cont[1:].max())}
+
+
+def ann_measurement(peak):
+    """The A-NN comparison scheme (Sec. 4.1, Remark rem:WG) beside AD-LBR on
+    the GPU: Fig. Radius (largest stencil radius over 3600 orientations at
+    kappa = 10, both schemes built by the library), and build and operator
+    times on a 2048^2 smooth field (kappa <= 10, F16 weights, FP32 u)."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    out = {}
+    th = np.linspace(0, np.pi, 3600, endpoint=False)
+    D = torch.from_numpy(synth.D_from_angle(th, 10.0).reshape(3, -1)).cuda()
+    g = ab.grid((1, th.size))
+    for name, sch in (("adlbr", ab.SCHEME_ADLBR), ("ann", ab.SCHEME_ANN)):
+        h = ab.adlbr_build_stencils_scheme(g, D, ab.F64, ab.F64, sch)
+        try:
+            offs = torch.zeros((th.size, 3, 2), dtype=torch.int16, device="cuda")
+            w = torch.zeros((th.size, 3), dtype=torch.float64, device="cuda")
+            ab.adlbr_stencils_export(h, offs, w)
+            out["fig_radius_max_" + name] = float(offs.double().pow(2).sum(-1).sqrt().max())
+        finally:
+            ab.adlbr_stencils_destroy(h)
+    n = 2048
+    Ds = torch.from_numpy(synth.smooth_field2d(n, n, 3, 1.0, 10.0, 16).reshape(3, -1).astype(np.float32)).cuda()
+    gg = ab.grid((n, n))
+    u = torch.rand(n * n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    Au = torch.empty_like(u)
+    st = torch.cuda.current_stream()
+    for name, sch in (("adlbr", ab.SCHEME_ADLBR), ("ann", ab.SCHEME_ANN)):
+        h = ab.adlbr_build_stencils_scheme(gg, Ds, ab.F32, ab.F16, sch)
+        try:
+            ab.adlbr_stencils_check(h)
+            bms = time_ms(lambda: ab.adlbr_build_stencils_scheme(gg, Ds, ab.F32, ab.F16, sch, out=h), 10, st)
+            ams = time_ms(lambda: ab.adlbr_apply(h, u, Au, ab.F32), 20, st)
+            offs = torch.zeros((n * n, 3, 2), dtype=torch.int16, device="cuda")
+            w = torch.zeros((n * n, 3), dtype=torch.float32, device="cuda")
+            ab.adlbr_stencils_export(h, offs, w)
+            r = offs.double().pow(2).sum(-1).sqrt().max(-1).values
+            out[name + "_2048"] = {"build_ms": bms, "apply_ms": ams, "apply_gpts": n * n / (ams * 1e-3) / 1e9,
+                                   "radius_mean": float(r.mean()), "radius_max": float(r.max())}
+            del offs, w
+        finally:
+            ab.adlbr_stencils_destroy(h)
+    out["field_2048"] = "smooth orientation, kappa in [1, 10], 16x16 lattice, seed 3"
+    return out
 
 
 def ced3d_measurement(steps=20, precond=2):
@@ -912,6 +959,7 @@ def main():
         plain = ced3d_measurement(precond=0)
         ced3d["plain_cg"] = {k: plain[k] for k in ("ms_per_step", "implicit_ms", "cg_iters_mean", "rms_to_clean")}
     spectral_study = None if args.no_spectral or rank != 0 else spectral_measurement()
+    ann_study = None if args.no_ann or rank != 0 else ann_measurement(peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -938,7 +986,7 @@ def main():
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
                 "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch,
-                "ced3d": ced3d, "spectral": spectral_study}
+                "ced3d": ced3d, "spectral": spectral_study, "ann": ann_study}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:

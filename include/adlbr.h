@@ -104,6 +104,36 @@ const char *adlbr_last_error(void);
 adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
                                   adlbr_dtype w_t, adlbr_stencils **out, cudaStream_t stream);
 
+/*
+ * Stencil schemes.  ADLBR_SCHEME_ADLBR is the method of the paper (the
+ * stencils of adlbr_build_stencils).  ADLBR_SCHEME_ANN is the paper's
+ * comparison scheme A-NN, the axes-directed non-negative six-point scheme of
+ * Sec. 4.1, Remark rem:WG (2D only): for D = [[a, b], [b, c]] the stencil
+ * {(+-1, 0), (0, +-1), +-(p, q)} with 2 gamma(+-1, 0) = a - (p/q) b,
+ * 2 gamma(0, +-1) = c - (q/p) b, 2 gamma(+-(p, q)) = b / (p q), where p, q are
+ * non-zero integers with b p q >= 0, |b|/c <= |p/q| <= a/|b| (Eq. ineqPQ) and
+ * max(|p|, |q|) minimal (the simplest fraction of that interval, unique;
+ * every comparison is an exact sign); b = 0 gives the four-point stencil.
+ * Its radius can reach the order of kappa^2 (Remark "Stencil radius").
+ */
+typedef enum { ADLBR_SCHEME_ADLBR = 0, ADLBR_SCHEME_ANN = 1 } adlbr_scheme;
+
+/*
+ * adlbr_build_stencils_scheme -- adlbr_build_stencils for the given scheme
+ * (arguments and error rules as there; |p|, |q| > 2047 is ADLBR_E_RANGE for
+ * A-NN).  An A-NN handle works with adlbr_apply, the explicit and implicit
+ * steps (CG and Jacobi-PCG), adlbr_stencils_export (the canonical half-
+ * stencil, as for AD-LBR) and adlbr_stencils_max_diag; the learned
+ * preconditioner, the gather form and the batched step take AD-LBR handles
+ * only (ADLBR_E_ARG otherwise).
+ */
+adlbr_status adlbr_build_stencils_scheme(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
+                                         adlbr_dtype w_t, int scheme, adlbr_stencils **out,
+                                         cudaStream_t stream);
+
+/* The scheme of a handle (adlbr_scheme). */
+adlbr_status adlbr_stencils_scheme(const adlbr_stencils *s, int *scheme);
+
 /* Synchronises `stream`, returns the handle's sticky build status
  * (ADLBR_OK, ADLBR_E_NONFINITE, ADLBR_E_NOT_SPD, ADLBR_E_RANGE,
  * ADLBR_E_NOT_CONVERGED, or ADLBR_E_TIMEOUT when an operator kernel on this

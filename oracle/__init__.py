@@ -17,6 +17,7 @@ Non-Negative Stencils for Anisotropic Diffusion", that it follows):
   (Eq. elliptic, solved "using Conjugate Gradient").
 * ``ced`` (module) -- the coherence-enhancing diffusion tensor, Sec. 4.4.
 * ``unet`` (module) -- the learned preconditioner's network (not in the paper).
+* ``ann`` (module) -- the A-NN comparison scheme, Sec. 4.1, Remark rem:WG.
 
 All floating point is FP64.
 """

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libadlbr.so")
 F64, F32, F16, BF16 = 0, 1, 2, 3
 NEUMANN, PERIODIC = 0, 1
 OP_AUTO, OP_SCATTER, OP_GATHER = 0, 1, 2
+SCHEME_ADLBR, SCHEME_ANN = 0, 1
 
 STATUS = {0: "OK", 1: "E_ARG", 2: "E_SHAPE", 3: "E_NOT_SPD", 4: "E_NONFINITE",
           5: "E_NOT_CONVERGED", 6: "E_TIMEOUT", 7: "E_CUDA", 8: "E_RANGE", 9: "E_INTERNAL"}
@@ -58,6 +59,9 @@ def lib():
             "adlbr_build_stencils": (_i32, [ctypes.POINTER(Grid), _vp, _i32, _i32,
                                             ctypes.POINTER(_vp), _vp]),
             "adlbr_stencils_check": (_i32, [_vp, _vp]),
+            "adlbr_build_stencils_scheme": (_i32, [ctypes.POINTER(Grid), _vp, _i32, _i32, _i32,
+                                                   ctypes.POINTER(_vp), _vp]),
+            "adlbr_stencils_scheme": (_i32, [_vp, ctypes.POINTER(_i32)]),
             "adlbr_stencils_grid": (_i32, [_vp, ctypes.POINTER(Grid)]),
             "adlbr_stencils_export": (_i32, [_vp, _vp, _vp, _vp]),
             "adlbr_stencils_destroy": (_i32, [_vp]),
@@ -153,6 +157,20 @@ def adlbr_build_stencils(g, D, D_t, w_t, out=None, stream=None):
     _check(lib().adlbr_build_stencils(ctypes.byref(g), _ptr(D), D_t, w_t, ctypes.byref(h),
                                       _stream(stream)))
     return h.value
+
+
+def adlbr_build_stencils_scheme(g, D, D_t, w_t, scheme, out=None, stream=None):
+    """adlbr_build_stencils for scheme SCHEME_ADLBR or SCHEME_ANN; returns the handle."""
+    h = _vp(out)
+    _check(lib().adlbr_build_stencils_scheme(ctypes.byref(g), _ptr(D), D_t, w_t, int(scheme), ctypes.byref(h),
+                                             _stream(stream)))
+    return h.value
+
+
+def adlbr_stencils_scheme(h):
+    v = _i32(0)
+    _check(lib().adlbr_stencils_scheme(h, ctypes.byref(v)))
+    return v.value
 
 
 def adlbr_stencils_check(h, stream=None):

@@ -55,14 +55,15 @@ static int64_t npoints(const adlbr_grid *g) {
     return g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
 }
 
-// *ps == NULL: allocates a handle for grid g and weight type w_t.
+// *ps == NULL: allocates a handle for grid g, weight type w_t and scheme.
 // *ps != NULL: checks that it matches (and takes g's boundary rule).
-static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_stencils **ps) {
+static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_stencils **ps,
+                                   int scheme = ADLBR_SCHEME_ADLBR) {
     adlbr_stencils *s = *ps;
     if (s) {
         bool same = s->dim == g->dim && s->w_t == w_t && s->n[0] == g->n[0] && s->n[1] == g->n[1] &&
-                    (g->dim == 2 || s->n[2] == g->n[2]);
-        if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type");
+                    (g->dim == 2 || s->n[2] == g->n[2]) && s->scheme == scheme;
+        if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type / scheme");
         if (s->bc != g->bc) pull_free(s);
         s->bc = g->bc;
         // the stencils are about to change: the gather table no longer matches
@@ -79,10 +80,12 @@ static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_s
     s->n[2] = g->dim == 3 ? g->n[2] : 1;
     s->N = npoints(g);
     s->w_t = w_t;
+    s->scheme = scheme;
     cudaGetDevice(&s->device);
     size_t ob = offs_bytes_per_point(s->dim) * (size_t)s->N;
     size_t wb = w_bytes_per_point(s->dim, w_t) * (size_t)s->N;
     cudaError_t e = cudaMalloc(&s->offs, ob);
+    if (e == cudaSuccess && scheme == ADLBR_SCHEME_ANN) e = cudaMalloc(&s->offs3, sizeof(short2) * (size_t)s->N);
     if (e == cudaSuccess) e = cudaMalloc(&s->w, wb);
     if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&s->err_host, sizeof(int));
@@ -109,14 +112,25 @@ int adlbr_last_residual_met(void) { return g_residual_met; }
 
 adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
                                   adlbr_dtype w_t, adlbr_stencils **out, cudaStream_t stream) {
+    return adlbr_build_stencils_scheme(g, D, D_t, w_t, ADLBR_SCHEME_ADLBR, out, stream);
+}
+
+adlbr_status adlbr_build_stencils_scheme(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
+                                         adlbr_dtype w_t, int scheme, adlbr_stencils **out,
+                                         cudaStream_t stream) {
     if (!out || !D) return fail(ADLBR_E_ARG, "null argument");
     if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "invalid grid");
     if (D_t != ADLBR_F32 && D_t != ADLBR_F64) return fail(ADLBR_E_ARG, "D must be F32 or F64");
     if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
         return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
+    if (scheme != ADLBR_SCHEME_ADLBR && scheme != ADLBR_SCHEME_ANN)
+        return fail(ADLBR_E_ARG, "unknown scheme %d", scheme);
+    if (scheme == ADLBR_SCHEME_ANN && g->dim != 2) return fail(ADLBR_E_SHAPE, "the A-NN scheme is 2D");
     adlbr_stencils *s = *out;
-    if (adlbr_status e = acquire_handle(g, w_t, &s)) return e;
-    adlbr_status st = s->dim == 2 ? launch_build2d(s, D, D_t, stream) : launch_build3d(s, D, D_t, stream);
+    if (adlbr_status e = acquire_handle(g, w_t, &s, scheme)) return e;
+    adlbr_status st = scheme == ADLBR_SCHEME_ANN ? launch_build_ann2d(s, D, D_t, stream)
+                      : s->dim == 2              ? launch_build2d(s, D, D_t, stream)
+                                                 : launch_build3d(s, D, D_t, stream);
     if (st != ADLBR_OK) {
         if (!*out) adlbr_stencils_destroy(s);
         return st;
@@ -136,6 +150,13 @@ adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream) {
     if (bits & ERRBIT_RANGE) return fail(ADLBR_E_RANGE, "stencil offset out of storage range");
     if (bits & ERRBIT_NOT_CONVERGED) return fail(ADLBR_E_NOT_CONVERGED, "reduction did not converge");
     if (bits & ERRBIT_TIMEOUT) return fail(ADLBR_E_TIMEOUT, "a device-side wait for a tile copy gave up");
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_stencils_scheme(const adlbr_stencils *s, int *scheme) {
+    if (adlbr_status st = check_handle(s)) return st;
+    if (!scheme) return fail(ADLBR_E_ARG, "null output");
+    *scheme = s->scheme;
     return ADLBR_OK;
 }
 
@@ -160,6 +181,7 @@ adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void 
 adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
     if (!s) return ADLBR_OK;
     if (s->offs) cudaFree(s->offs);
+    if (s->offs3) cudaFree(s->offs3);
     if (s->w) cudaFree(s->w);
     if (s->err) cudaFree(s->err);
     if (s->err_host) cudaFreeHost(s->err_host);

@@ -27,25 +27,27 @@ using op::wrap;
 template <int TW, int TH, int NT, int WX, bool F16W>
 __global__ void __launch_bounds__(NT) apply2d_tiled_tma(int nx, int ny, int bc, float scale,
                                                         const short4 *__restrict__ offs,
+                                                        const short2 *__restrict__ offs3,
                                                         const void *__restrict__ wbase, adlbr_dtype wt,
                                                         const float *__restrict__ u, float *__restrict__ acc,
                                                         const int *__restrict__ skip,
                                                         const __grid_constant__ CUtensorMap map, int *err) {
     extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
-    op::tile2d<float, TW, TH, NT, WX, F16W, true>(nx, ny, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TW,
+    op::tile2d<float, TW, TH, NT, WX, F16W, true>(nx, ny, bc, scale, offs, offs3, wbase, wt, u, acc, blockIdx.x * TW,
                                                   blockIdx.y * TH, smem, &map, err);
 }
 
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W>
 __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, float scale,
                                                     const short4 *__restrict__ offs,
+                                                    const short2 *__restrict__ offs3,
                                                     const void *__restrict__ wbase, adlbr_dtype wt,
                                                     const UT *__restrict__ u, float *__restrict__ acc,
                                                     const int *__restrict__ skip) {
     extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
-    op::tile2d<UT, TW, TH, NT, WX, F16W>(nx, ny, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TW,
+    op::tile2d<UT, TW, TH, NT, WX, F16W>(nx, ny, bc, scale, offs, offs3, wbase, wt, u, acc, blockIdx.x * TW,
                                          blockIdx.y * TH, smem);
 }
 
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, floa
 template <typename UT, typename AT = typename UTraits<UT>::acc>
 __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, AT scale,
                                                        const short4 *__restrict__ offs,
+                                                       const short2 *__restrict__ offs3,
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
                                                        const UT *__restrict__ u, AT *__restrict__ Au) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,8 +65,8 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, A
     const short4 o = offs[z];
     AT w[3];
     load_weights<AT, 3>(wbase, wt, z, w);
-    const int ex[3] = {o.x, o.z, -o.x - o.z};
-    const int ey[3] = {o.y, o.w, -o.y - o.w};
+    int ex[3], ey[3];
+    offsets2d(o, offs3, z, ex, ey);
     const AT uz = to_acc(u[z]);
     AT acc = 0;
 #pragma unroll
@@ -188,12 +191,13 @@ __device__ __forceinline__ void write_canonical(int (&v)[K][DIM], double (&w)[K]
 }
 
 template <typename WO>
-__global__ void export2d_kernel(int64_t N, const short4 *__restrict__ offs, const void *wbase,
-                                adlbr_dtype wt, int16_t *out_offs, WO *out_w) {
+__global__ void export2d_kernel(int64_t N, const short4 *__restrict__ offs, const short2 *__restrict__ offs3,
+                                const void *wbase, adlbr_dtype wt, int16_t *out_offs, WO *out_w) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    short4 o = offs[i];
-    int v[3][2] = {{o.x, o.y}, {o.z, o.w}, {-o.x - o.z, -o.y - o.w}};
+    int ex[3], ey[3];
+    offsets2d(offs[i], offs3, i, ex, ey);
+    int v[3][2] = {{ex[0], ey[0]}, {ex[1], ey[1]}, {ex[2], ey[2]}};
     double w[3];
     unsigned zm = load_weights<double, 3>(wbase, wt, i, w);
     write_canonical<2, 3, WO>(v, w, zm, out_offs, out_w, i);
@@ -219,11 +223,13 @@ adlbr_status launch_export(const adlbr_stencils *s, int16_t *offs, void *w, cuda
     unsigned blocks = blocks_for(s->N, threads);
     if (s->dim == 2) {
         if (s->w_t == ADLBR_F64)
-            export2d_kernel<double><<<blocks, threads, 0, st>>>(s->N, (const short4 *)s->offs, s->w,
-                                                                s->w_t, offs, (double *)w);
+            export2d_kernel<double><<<blocks, threads, 0, st>>>(s->N, (const short4 *)s->offs,
+                                                                (const short2 *)s->offs3, s->w, s->w_t, offs,
+                                                                (double *)w);
         else
-            export2d_kernel<float><<<blocks, threads, 0, st>>>(s->N, (const short4 *)s->offs, s->w,
-                                                               s->w_t, offs, (float *)w);
+            export2d_kernel<float><<<blocks, threads, 0, st>>>(s->N, (const short4 *)s->offs,
+                                                               (const short2 *)s->offs3, s->w, s->w_t, offs,
+                                                               (float *)w);
     } else {
         if (s->w_t == ADLBR_F64)
             export3d_kernel<double><<<blocks, threads, 0, st>>>(s->N, (const char4 *)s->offs, s->w,
@@ -253,25 +259,25 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
                                    T::WH)) {
                 if (s->w_t == ADLBR_F16)
                     apply2d_tiled_tma<TW, TH, NT, WX, true><<<grid, NT, smem, st>>>(
-                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w, s->w_t,
+                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t,
                         reinterpret_cast<const float *>(u), acc, skip, map, s->err);
                 else
                     apply2d_tiled_tma<TW, TH, NT, WX, false><<<grid, NT, smem, st>>>(
-                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w, s->w_t,
+                        (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t,
                         reinterpret_cast<const float *>(u), acc, skip, map, s->err);
             } else if (s->w_t == ADLBR_F16)
                 apply2d_tiled<UT, TW, TH, NT, WX, true><<<grid, NT, smem, st>>>(
-                    (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w,
+                    (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w,
                     s->w_t, u, acc, skip);
             else
                 apply2d_tiled<UT, TW, TH, NT, WX, false><<<grid, NT, smem, st>>>(
-                    (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, s->w,
+                    (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w,
                     s->w_t, u, acc, skip);
         } else {
             const int threads = 256;
             dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
             apply2d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (AT)scale,
-                                                          (const short4 *)s->offs, s->w, s->w_t, u,
+                                                          (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t, u,
                                                           acc);
         }
     } else if constexpr (sizeof(AT) == 4) {
@@ -329,7 +335,7 @@ adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, doub
         const int threads = 256;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
         apply2d_scatter<float, double><<<grid, threads, 0, st>>>(
-            (int)s->n[0], (int)s->n[1], s->bc, scale, (const short4 *)s->offs, s->w, s->w_t, u, acc);
+            (int)s->n[0], (int)s->n[1], s->bc, scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t, u, acc);
     } else {
         const int threads = 128;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);

@@ -96,11 +96,11 @@ __global__ void __launch_bounds__(BNT) batch_accumulate_kernel(const adlbr_batch
         if (it.dim == 2) {
             if (it.wt == ADLBR_F16)
                 op::tile2d<float, TW, TH, BNT, WX, true>(it.nx, it.ny, it.bc, it.scale,
-                                                         (const short4 *)it.offs, it.w, it.wt, it.u,
+                                                         (const short4 *)it.offs, nullptr, it.w, it.wt, it.u,
                                                          it.acc, tl.x0, tl.y0, smem);
             else
                 op::tile2d<float, TW, TH, BNT, WX, false>(it.nx, it.ny, it.bc, it.scale,
-                                                          (const short4 *)it.offs, it.w, it.wt, it.u,
+                                                          (const short4 *)it.offs, nullptr, it.w, it.wt, it.u,
                                                           it.acc, tl.x0, tl.y0, smem);
         } else if (it.wt == ADLBR_F16) {
             op::tile3d<float, BX, BY, BZ, true>(it.nx, it.ny, it.nz, it.bc, it.scale, (const char4 *)it.offs,
@@ -264,6 +264,10 @@ adlbr_status adlbr_batch_create(int n_items, adlbr_stencils *const *s, float *co
         if (h->device != dev) {
             free_batch(b);
             return fail(ADLBR_E_ARG, "item %d lives on device %d, current device is %d", i, h->device, dev);
+        }
+        if (h->scheme != ADLBR_SCHEME_ADLBR) {
+            free_batch(b);
+            return fail(ADLBR_E_ARG, "item %d: the batched step takes AD-LBR stencils", i);
         }
         adlbr_batch_item it = {};
         it.dim = h->dim;

@@ -73,6 +73,8 @@ struct adlbr_stencils {
     adlbr_dtype w_t;
     int device;
     void *offs;        // device
+    void *offs3;       // device, 2D general stencils (A-NN) only: the third offset, short2 per point
+    int scheme;        // adlbr_scheme
     void *w;           // device
     int *err;          // device, sticky error bits
     int *err_host;     // pinned host mirror
@@ -141,6 +143,21 @@ template <> __device__ __forceinline__ __half from_acc<__half>(float v) {
 }
 template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float v) {
     return __ushort_as_bfloat16(f2bf_bits(v));
+}
+
+// The three half-stencil offsets of 2D point z.  An AD-LBR stencil stores the
+// superbase (e0, e1) and e2 = -e0 - e1 (Corollary
+// ObtuseSuperBaseFromReducedBasis2); a general stencil (the A-NN scheme of
+// Remark rem:WG) stores e2 in its own plane offs3.
+__device__ __forceinline__ void offsets2d(short4 o, const short2 *__restrict__ offs3, int64_t z, int (&ex)[3],
+                                          int (&ey)[3]) {
+    ex[0] = o.x, ey[0] = o.y, ex[1] = o.z, ey[1] = o.w;
+    if (offs3) {
+        const short2 t = offs3[z];
+        ex[2] = t.x, ey[2] = t.y;
+    } else {
+        ex[2] = -o.x - o.z, ey[2] = -o.y - o.w;
+    }
 }
 
 // Selling offsets of a 3D superbase (e0 = -e1-e2-e3): pair q = (i, j) gets
@@ -235,6 +252,8 @@ adlbr_status check_handle(const adlbr_stencils *s);
 // kernels' host launchers
 adlbr_status launch_build2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st);
 adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st);
+// the A-NN comparison scheme (Sec. 4.1, Remark rem:WG), 2D (ann.cu)
+adlbr_status launch_build_ann2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st);
 adlbr_status launch_export(const adlbr_stencils *s, int16_t *offs, void *w, cudaStream_t st);
 adlbr_status launch_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                           cudaStream_t st);

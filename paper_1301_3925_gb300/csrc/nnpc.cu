@@ -37,14 +37,15 @@ struct FcgState {
 
 // A_zz: every in-grid pair (z, z +- e_k) adds w_k at both ends
 __global__ void diag2d_kernel(int nx, int ny, int bc, const short4 *__restrict__ offs,
-                              const void *__restrict__ wbase, adlbr_dtype wt, float *__restrict__ d) {
+                              const short2 *__restrict__ offs3, const void *__restrict__ wbase, adlbr_dtype wt,
+                              float *__restrict__ d) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
     const int64_t z = (int64_t)y * nx + x;
-    const short4 o = offs[z];
     float w[3];
     load_weights<float, 3>(wbase, wt, z, w);
-    const int ex[3] = {o.x, o.z, -o.x - o.z}, ey[3] = {o.y, o.w, -o.y - o.w};
+    int ex[3], ey[3];
+    offsets2d(offs[z], offs3, z, ex, ey);
     float own = 0.f;
     for (int k = 0; k < 3; ++k) {
         if (w[k] == 0.f) continue;
@@ -528,7 +529,7 @@ static adlbr_status compute_diag(adlbr_stencils *s, NnWorkspace &W, double dt, d
     ADLBR_CUDA(cudaMemsetAsync(W.dmax, 0, sizeof(unsigned), st));
     dim3 g(blocks_for(s->n[0], 256), (unsigned)s->n[1]);
     if (s->dim == 2)
-        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs,
+        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs, (const short2 *)s->offs3,
                                          s->w, s->w_t, W.d);
     else
         diag3d_kernel<<<dim3(blocks_for(s->n[0], 128), (unsigned)s->n[1], (unsigned)s->n[2]), 128, 0, st>>>(
@@ -556,7 +557,7 @@ adlbr_status launch_jacobi_inverse(const adlbr_stencils *s, double dt, float *in
     ADLBR_CUDA(cudaMemsetAsync(inv_d, 0, s->N * sizeof(float), st));
     if (s->dim == 2) {
         dim3 g(blocks_for(s->n[0], 256), (unsigned)s->n[1]);
-        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs, s->w,
+        diag2d_kernel<<<g, 256, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (const short4 *)s->offs, (const short2 *)s->offs3, s->w,
                                          s->w_t, inv_d);
     } else {
         diag3d_kernel<<<dim3(blocks_for(s->n[0], 128), (unsigned)s->n[1], (unsigned)s->n[2]), 128, 0, st>>>(
@@ -570,6 +571,8 @@ adlbr_status launch_jacobi_inverse(const adlbr_stencils *s, double dt, float *in
 
 static adlbr_status check_nn_grid(const adlbr_stencils *s, const adlbr_unet *net) {
     if (s->dim != 2) return fail(ADLBR_E_SHAPE, "the learned preconditioner is 2D only");
+    if (s->scheme != ADLBR_SCHEME_ADLBR)
+        return fail(ADLBR_E_ARG, "the learned preconditioner's features are defined for AD-LBR stencils");
     if (s->n[0] % (RF * 4) || s->n[1] % (RF * 4))
         return fail(ADLBR_E_SHAPE, "grid extents must be multiples of %d for the preconditioner", RF * 4);
     int cin, B, H, Wd;

@@ -79,7 +79,8 @@ __device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z,
 }
 
 // acc += scale A u over the tile at (x0, y0); every thread of the block
-// calls it (block-wide barriers inside).  smem: 2 * WH * P floats, 16-byte
+// calls it (block-wide barriers inside).  offs3: the third offsets of a
+// general (A-NN) stencil, nullptr for AD-LBR.  smem: 2 * WH * P floats, 16-byte
 // aligned (128-byte for TMA).  TMA: the u window (FP32, non-periodic grid,
 // nx % 4 == 0) arrives as one bulk tensor copy of the map's WW x WH box;
 // cells outside the grid are zero-filled, as the plain staging leaves them.
@@ -88,7 +89,8 @@ __device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z,
 // waits up to four more bounds for the copy to land, and returns.
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W, bool TMA = false>
 __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, const short4 *__restrict__ offs,
-                                       const void *__restrict__ wbase, adlbr_dtype wt,
+                                       const short2 *__restrict__ offs3, const void *__restrict__ wbase,
+                                       adlbr_dtype wt,
                                        const UT *__restrict__ u, float *__restrict__ acc, int x0, int y0,
                                        float *smem, const CUtensorMap *map = nullptr, int *err = nullptr) {
     using T = Tile<TW, TH, NT, WX>;
@@ -174,7 +176,8 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
 #pragma unroll
             for (int i = 0; i < 3; ++i) w[i] *= scale;
         }
-        const int ex[3] = {o.x, o.z, -o.x - o.z}, ey[3] = {o.y, o.w, -o.y - o.w};
+        int ex[3], ey[3];
+        offsets2d(o, offs3, z, ex, ey);
         const int zw = (ly + HALO) * P + tx + HALO;
         const float uz = uw[zw];
         float own = 0.f;

@@ -599,7 +599,7 @@ adlbr_status launch_pull_u(const adlbr_stencils *s, const UT *u, OT *out, float 
 // ---------------------------------------------------------------- host side
 bool pull_supported(const adlbr_stencils *s) {
     // extras are counted in uint32: at most 6 per point
-    return s->dim == 2 && s->w_t == ADLBR_F16 && s->N <= (int64_t)1 << 29;
+    return s->dim == 2 && s->scheme == ADLBR_SCHEME_ADLBR && s->w_t == ADLBR_F16 && s->N <= (int64_t)1 << 29;
 }
 
 void pull_free(adlbr_stencils *s) {

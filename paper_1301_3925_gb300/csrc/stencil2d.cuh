@@ -18,6 +18,8 @@
 // agree bit for bit with any other exact construction.
 #pragma once
 
+#include <type_traits>
+
 #include "exact.cuh"
 #include "internal.cuh"
 #include "store.cuh"
@@ -99,6 +101,29 @@ __device__ __forceinline__ float gramf(float sxx, float sxy, float syy, float ux
     return sxx * ux * vx + sxy * (ux * vy + uy * vx) + syy * uy * vy;
 }
 
+// Sign of sum_k n_k x_k (the Gram value <u, S v>) and its value, for weights
+// stored as F16 (FAST): the FP32 sum of the rounded products, whose error is
+// below 3 u A (u = 2^-24, A = sum |n_k x_k|; bound taken as 4 u A), settles
+// the sign when |v| exceeds the bound and gives the value to 2^-14 relative
+// when |v| exceeds 2^14 times it -- far below the F16 rounding of the stored
+// weight.  Otherwise, and for every other storage, the float-float
+// evaluation with its exact fallback (sign_value) decides.
+template <bool FAST, typename T>
+__device__ __forceinline__ int sign_value_w(const T (&x)[3], const int (&n)[3], typename WVal<T>::type &val) {
+    if constexpr (FAST && std::is_same<T, float>::value) {
+        const float p0 = __fmul_rn((float)n[0], x[0]), p1 = __fmul_rn((float)n[1], x[1]),
+                    p2 = __fmul_rn((float)n[2], x[2]);
+        const float v = __fadd_rn(__fadd_rn(p0, p1), p2);
+        const float A = __fadd_rn(__fadd_rn(fabsf(p0), fabsf(p1)), fabsf(p2));
+        const float bound = __fmaf_rn(A, 0x1p-22f, 0x1p-120f);
+        if (fabsf(v) > __fmul_rn(bound, 0x1p14f)) {
+            val = FF{v, 0.f};
+            return v > 0.f ? 1 : -1;
+        }
+    }
+    return sign_value<3>(x, n, val);
+}
+
 constexpr int kMaxReduce = 64;
 constexpr int kMaxFix = 256;
 // |coordinates| <= 2047 keeps every integer of the predicates below 2^24
@@ -107,7 +132,8 @@ constexpr int kMaxCoord = 2047;
 }  // namespace s2d
 
 // Builds and stores the stencil of point i from D = [[a, b], [b, c]].
-template <typename T>
+// F16W: the weights are stored as F16 (sign_value_w's FP32 filter).
+template <typename T, bool F16W = false>
 __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
                                               void *wbase, adlbr_dtype wt, int *err) {
     using namespace s2d;
@@ -132,21 +158,28 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
     // certified exactly below, so these shortcuts can only cost repair steps)
     float sxx, sxy, syy;
     scaled_adj(a, b, c, sxx, sxy, syy);
+    // The Gram values of the running basis are updated, not recomputed:
+    // f' = e - q f gives |f'|^2 = |e|^2 - q (2 <e,f> - q |f|^2) and
+    // <f, f'> = <e,f> - q |f|^2.
     float ex = 1.f, ey = 0.f, fx = 0.f, fy = 1.f;
-    float gff = syy;   // |f|_S^2 of f = (0, 1)
+    float gee = sxx, gef = sxy, gff = syy;   // Gram values of e = (1, 0), f = (0, 1)
     for (int it = 0; it < kMaxReduce; ++it) {
         if (!(gff > 0.f)) break;
-        const float gef = gramf(sxx, sxy, syy, ex, ey, fx, fy);
         const float q = fminf(fmaxf(rintf(__fdividef(gef, gff)), -2048.f), 2048.f);
         const float nx = fmaf(-q, fx, ex), ny = fmaf(-q, fy, ey);   // exact: integers below 2^24
-        const float gee = gff;
+        if (fabsf(nx) > (float)kMaxCoord || fabsf(ny) > (float)kMaxCoord) {
+            ex = fx, ey = fy, fx = nx, fy = ny;
+            break;
+        }
+        const float gnn = fmaf(-q, fmaf(-q, gff, 2.f * gef), gee);
+        const float gfn = fmaf(-q, gff, gef);
+        const bool shorter = gff > gnn;
         ex = fx, ey = fy, fx = nx, fy = ny;
-        if (fabsf(fx) > (float)kMaxCoord || fabsf(fy) > (float)kMaxCoord) break;
-        gff = gramf(sxx, sxy, syy, fx, fy, fx, fy);
-        if (!(gee > gff)) break;
+        gee = gff, gef = gfn, gff = gnn;
+        if (!shorter) break;
     }
     // (ii) orientation of f
-    if (gramf(sxx, sxy, syy, ex, ey, fx, fy) > 0.f) fx = -fx, fy = -fy;
+    if (gef > 0.f) fx = -fx, fy = -fy;
     V2 e{(int)ex, (int)ey}, f{(int)fx, (int)fy};
 
     // (iii) superbase, certified and repaired with exact signs
@@ -161,7 +194,7 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
             T x[3];
             int n[3];
             terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
-            sg[k] = sign_value<3>(x, n, val[k]);
+            sg[k] = sign_value_w<F16W>(x, n, val[k]);
             if (sg[k] > 0 && bad < 0) bad = k;
         }
         if (bad < 0) {

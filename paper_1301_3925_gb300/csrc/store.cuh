@@ -40,8 +40,13 @@ __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64
         __half h[L];
 #pragma unroll
         for (int k = 0; k < L; ++k) h[k] = __ushort_as_half((unsigned short)0);
+        // wf[k] * inv lies in [0, 1): the rounding of f2h_bits without its
+        // sign and overflow cases (round to nearest even, subnormals too)
 #pragma unroll
-        for (int k = 0; k < K; ++k) h[k] = __ushort_as_half(f2h_bits(wf[k] * inv));
+        for (int k = 0; k < K; ++k) {
+            const uint32_t bb = __float_as_uint(__fmul_rn(__fmul_rn(wf[k], inv), 0x1p-112f));
+            h[k] = __ushort_as_half((unsigned short)((bb + 0x0fffu + ((bb >> 13) & 1u)) >> 13));
+        }
         uint16_t meta = (uint16_t)((zmask & 0xffu) | ((unsigned)(uint8_t)(int8_t)s << 8));
         *reinterpret_cast<uint16_t *>(&h[K]) = meta;
         if (L == 4)
