@@ -7,7 +7,8 @@
 // Eq. DSum3D): offsets e_k x e_l with weights -<e_i, D e_j>/2.
 //
 // GPU design, as in 2D: the reduction and MakeObtuse run in FP32 on a
-// rescaled D; the resulting superbase is certified with exact signs of the
+// rescaled D, in Gram-matrix form (integer vectors, FP32 Gram values updated
+// with them); the resulting superbase is certified with exact signs of the
 // six products <e_i, D e_j> (exact.cuh) and repaired, while a product is
 // positive, by Selling steps (e_i, e_j, e_k, e_l) -> (-e_i, e_j, e_k + e_i,
 // e_l + e_i), each lowering sum |e|_D^2 by 2 <e_i, D e_j>.  The certified
@@ -94,19 +95,15 @@ __device__ __forceinline__ bool spd3(const float (&D)[6]) {
     return spd64(a, b, c, xy, xz, yz);
 }
 
-// Lagrange reduction of (e, f) for the FP32 form d; on exit |e| <= |f|.
-__device__ __forceinline__ void lagrange_f(const float (&d)[6], V3 &e, V3 &f) {
-    for (int it = 0; it < 48; ++it) {
-        float den = g3(d, f, f);
-        if (!(den > 0.f)) break;
-        float r = rintf(g3(d, e, f) / den);
-        r = fminf(fmaxf(r, -256.f), 256.f);
-        V3 nf = sub(e, mul((int)r, f));
-        e = f;
-        f = nf;
-        if (amax(f) > 4 * kMaxCoord) break;
-        if (!(g3(d, e, e) > g3(d, f, f))) break;
-    }
+// The Gram matrix of the basis b for the FP32 form d: G[i][j] = <b_i, d b_j>.
+__device__ __forceinline__ void gram3(const float (&d)[6], const V3 (&b)[3], float (&G)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            G[i][j] = g3(d, b[i], b[j]);
+            G[j][i] = G[i][j];
+        }
 }
 
 template <typename T>
@@ -139,54 +136,86 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     float d[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) d[k] = (float)(D[k] / dmax);
+    // The basis vectors are exact integers; their Gram values are carried in
+    // FP32 and updated with the vectors (f' = e - q f changes |f|^2 and the
+    // products with the third vector linearly), and recomputed from the
+    // vectors once per round.  The result is certified exactly below, so the
+    // rounding of these values can only cost repair steps.
     V3 b[3] = {V3{1, 0, 0}, V3{0, 1, 0}, V3{0, 0, 1}};
     for (int it = 0; it < 24; ++it) {
-        // sort by norm
-        float nb[3] = {g3(d, b[0], b[0]), g3(d, b[1], b[1]), g3(d, b[2], b[2])};
+        float G[3][3];
+        gram3(d, b, G);
+        // sort by norm (G follows the permutation)
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int q = 0; q < 2 - p; ++q)
-                if (nb[q + 1] < nb[q]) {
-                    float tn = nb[q];
-                    nb[q] = nb[q + 1];
-                    nb[q + 1] = tn;
+                if (G[q + 1][q + 1] < G[q][q]) {
+                    const int r = 3 - q - (q + 1);   // the third index
                     V3 tv = b[q];
                     b[q] = b[q + 1];
                     b[q + 1] = tv;
+                    float t = G[q][q];
+                    G[q][q] = G[q + 1][q + 1];
+                    G[q + 1][q + 1] = t;
+                    t = G[q][r];
+                    G[q][r] = G[r][q] = G[q + 1][r];
+                    G[q + 1][r] = G[r][q + 1] = t;
                 }
+        // Lagrange reduction of (e, f) = (b1, b0); h_e, h_f their products with b2
         V3 e = b[1], f = b[0];
-        lagrange_f(d, e, f);
+        float gee = G[1][1], gff = G[0][0], gef = G[0][1], he = G[1][2], hf = G[0][2];
+        for (int l = 0; l < 48; ++l) {
+            if (!(gff > 0.f)) break;
+            float r = rintf(gef / gff);
+            r = fminf(fmaxf(r, -256.f), 256.f);
+            const int ri = (int)r;
+            const V3 nf = sub(e, mul(ri, f));
+            const float gnn = fmaf(-r, fmaf(-r, gff, 2.f * gef), gee);
+            const float gfn = fmaf(-r, gff, gef);
+            const float hn = fmaf(-r, hf, he);
+            const bool shorter = gff > gnn;
+            e = f;
+            f = nf;
+            gee = gff, gef = gfn, gff = gnn, he = hf, hf = hn;
+            if (amax(f) > 4 * kMaxCoord) break;
+            if (!shorter) break;
+        }
         b[0] = e;
         b[1] = f;
-        // closest vector to b2 in b0 Z + b1 Z
-        float G00 = g3(d, b[0], b[0]), G01 = g3(d, b[0], b[1]), G11 = g3(d, b[1], b[1]);
-        float r0 = g3(d, b[0], b[2]), r1 = g3(d, b[1], b[2]);
-        float det = G00 * G11 - G01 * G01;
+        // closest vector to b2 in b0 Z + b1 Z, scored by
+        // |b2 - k0 b0 - k1 b1|^2 = G22 - 2 (k0 h0 + k1 h1) + k0^2 G00 + 2 k0 k1 G01 + k1^2 G11
+        const float G00 = gee, G01 = gef, G11 = gff, r0 = he, r1 = hf, G22 = G[2][2];
+        const float det = G00 * G11 - G01 * G01;
         if (!(det > 0.f)) break;
         float y0 = (G11 * r0 - G01 * r1) / det, y1 = (G00 * r1 - G01 * r0) / det;
         y0 = fminf(fmaxf(y0, -512.f), 512.f);
         y1 = fminf(fmaxf(y1, -512.f), 512.f);
-        int f0 = (int)floorf(y0), f1 = (int)floorf(y1);
-        V3 best{0, 0, 0};
+        const int f0 = (int)floorf(y0), f1 = (int)floorf(y1);
+        int bk0 = 0, bk1 = 0;
         float bestn = 3.4e38f;
-        for (int k0 = f0 - 1; k0 <= f0 + 2; ++k0)
-            for (int k1 = f1 - 1; k1 <= f1 + 2; ++k1) {
-                V3 c = add(mul(k0, b[0]), mul(k1, b[1]));
-                V3 t = sub(b[2], c);
-                float nt = g3(d, t, t);
+#pragma unroll
+        for (int k0 = -1; k0 <= 2; ++k0)
+#pragma unroll
+            for (int k1 = -1; k1 <= 2; ++k1) {
+                const float a0 = (float)(f0 + k0), a1 = (float)(f1 + k1);
+                const float nt = fmaf(a0, fmaf(a0, G00, fmaf(2.f * a1, G01, -2.f * r0)),
+                                      fmaf(a1, fmaf(a1, G11, -2.f * r1), G22));
                 if (nt < bestn) {
                     bestn = nt;
-                    best = c;
+                    bk0 = f0 + k0;
+                    bk1 = f1 + k1;
                 }
             }
-        b[2] = sub(b[2], best);
+        b[2] = sub(b[2], add(mul(bk0, b[0]), mul(bk1, b[1])));
         if (amax(b[2]) > 4 * kMaxCoord) break;
-        if (g3(d, b[2], b[2]) >= g3(d, b[1], b[1])) break;
+        if (bestn >= G11) break;
     }
 
     // ---- Prop. MakeObtuse (approximate decisions) ----
-    float p01 = fabsf(g3(d, b[0], b[1])), p02 = fabsf(g3(d, b[0], b[2])), p12 = fabsf(g3(d, b[1], b[2]));
+    float Gf[3][3];
+    gram3(d, b, Gf);
+    float p01 = fabsf(Gf[0][1]), p02 = fabsf(Gf[0][2]), p12 = fabsf(Gf[1][2]);
     // the pair with the smallest |<.,D.>| is {b'1, b'2}; b'3 is the other vector,
     // b'2 the one of the pair whose product with b'3 is larger
     int i1, i2, i3;
@@ -201,10 +230,11 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
         if (p01 <= p02) { i1 = 1; i2 = 2; } else { i1 = 2; i2 = 1; }
     }
     V3 b1 = b[i1], b2 = b[i2], b3 = b[i3];
-    if (g3(d, b1, b3) > 0.f) b1 = neg(b1);
-    if (g3(d, b2, b3) > 0.f) b2 = neg(b2);
+    float s13 = Gf[i1][i3], s23 = Gf[i2][i3], s12 = Gf[i1][i2];
+    if (s13 > 0.f) b1 = neg(b1), s12 = -s12;
+    if (s23 > 0.f) b2 = neg(b2), s12 = -s12;
     V3 e[4];
-    if (g3(d, b1, b2) <= 0.f) {
+    if (s12 <= 0.f) {
         e[1] = b1;
         e[2] = b2;
         e[3] = b3;

@@ -18,8 +18,6 @@
 // agree bit for bit with any other exact construction.
 #pragma once
 
-#include <type_traits>
-
 #include "exact.cuh"
 #include "internal.cuh"
 #include "store.cuh"
@@ -101,29 +99,6 @@ __device__ __forceinline__ float gramf(float sxx, float sxy, float syy, float ux
     return sxx * ux * vx + sxy * (ux * vy + uy * vx) + syy * uy * vy;
 }
 
-// Sign of sum_k n_k x_k (the Gram value <u, S v>) and its value, for weights
-// stored as F16 (FAST): the FP32 sum of the rounded products, whose error is
-// below 3 u A (u = 2^-24, A = sum |n_k x_k|; bound taken as 4 u A), settles
-// the sign when |v| exceeds the bound and gives the value to 2^-14 relative
-// when |v| exceeds 2^14 times it -- far below the F16 rounding of the stored
-// weight.  Otherwise, and for every other storage, the float-float
-// evaluation with its exact fallback (sign_value) decides.
-template <bool FAST, typename T>
-__device__ __forceinline__ int sign_value_w(const T (&x)[3], const int (&n)[3], typename WVal<T>::type &val) {
-    if constexpr (FAST && std::is_same<T, float>::value) {
-        const float p0 = __fmul_rn((float)n[0], x[0]), p1 = __fmul_rn((float)n[1], x[1]),
-                    p2 = __fmul_rn((float)n[2], x[2]);
-        const float v = __fadd_rn(__fadd_rn(p0, p1), p2);
-        const float A = __fadd_rn(__fadd_rn(fabsf(p0), fabsf(p1)), fabsf(p2));
-        const float bound = __fmaf_rn(A, 0x1p-22f, 0x1p-120f);
-        if (fabsf(v) > __fmul_rn(bound, 0x1p14f)) {
-            val = FF{v, 0.f};
-            return v > 0.f ? 1 : -1;
-        }
-    }
-    return sign_value<3>(x, n, val);
-}
-
 constexpr int kMaxReduce = 64;
 constexpr int kMaxFix = 256;
 // |coordinates| <= 2047 keeps every integer of the predicates below 2^24
@@ -132,8 +107,7 @@ constexpr int kMaxCoord = 2047;
 }  // namespace s2d
 
 // Builds and stores the stencil of point i from D = [[a, b], [b, c]].
-// F16W: the weights are stored as F16 (sign_value_w's FP32 filter).
-template <typename T, bool F16W = false>
+template <typename T>
 __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
                                               void *wbase, adlbr_dtype wt, int *err) {
     using namespace s2d;
@@ -194,7 +168,7 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
             T x[3];
             int n[3];
             terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
-            sg[k] = sign_value_w<F16W>(x, n, val[k]);
+            sg[k] = sign_value<3>(x, n, val[k]);
             if (sg[k] > 0 && bad < 0) bad = k;
         }
         if (bad < 0) {
