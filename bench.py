@@ -580,9 +580,9 @@ def volume_measurement(peak, steps):
     """3D 256^3 needle field (eigenvalues 1, 1/400, 1/400, smooth random
     orientation on a 16^3 lattice, seed 2): stencil build, operator and
     explicit-step throughput, and the precision study: `steps` explicit steps
-    at dt = 1 / max A_zz with u in FP64, FP32 and BF16 (FP16 weights for the
-    FP32 / BF16 runs, FP64 weights for the FP64 run), errors relative to the
-    FP64 run."""
+    at dt = 1 / max A_zz with u in FP64, FP32, FP16 and BF16 (FP16 weights for
+    the FP32 / FP16 / BF16 runs, FP64 weights for the FP64 run), errors
+    relative to the FP64 run, and the error of one step."""
     import torch
     import synth
     from paper_1301_3925_gb300 import adlbr as ab
@@ -609,21 +609,33 @@ def volume_measurement(peak, steps):
         dt = 1.0 / ab.adlbr_stencils_max_diag(h64)
         out["dt"] = dt
         runs = {}
-        for name, h, dtype, code in (("f64", h64, torch.float64, ab.F64), ("f32", h16, torch.float32, ab.F32),
-                                     ("bf16", h16, torch.bfloat16, ab.BF16)):
-            u = torch.from_numpy(u0).cuda().to(dtype)
+        cases = (("f64", h64, torch.float64, ab.F64), ("f32", h16, torch.float32, ab.F32),
+                 ("f16", h16, torch.float16, ab.F16), ("bf16", h16, torch.bfloat16, ab.BF16))
+        u64 = torch.from_numpy(u0).cuda()
+        sc64 = torch.empty(ab.adlbr_step_scratch_bytes(h64, ab.F64), dtype=torch.uint8, device="cuda")
+        for name, h, dtype, code in cases:
+            u = u64.to(dtype, copy=True)
             scratch = torch.empty(ab.adlbr_step_scratch_bytes(h, code), dtype=torch.uint8, device="cuda")
+            # one step from the same (rounded) u^n against the FP64 step of it
+            u1, r1 = u.clone(), u.to(torch.float64, copy=True)
+            ab.adlbr_step_explicit(h, u1, scratch, code, dt, 1)
+            ab.adlbr_step_explicit(h64, r1, sc64, ab.F64, dt, 1)
+            torch.cuda.synchronize()
+            step_err = (u1.double() - r1).abs().max().item() / r1.abs().max().item()
+            ab.adlbr_step_explicit(h, u1, scratch, code, dt, 2)   # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ab.adlbr_step_explicit(h, u, scratch, code, dt, steps)
             torch.cuda.synchronize()
-            runs[name] = (u.double(), (time.perf_counter() - t0) * 1e3 / steps)
+            runs[name] = (u.double(), (time.perf_counter() - t0) * 1e3 / steps, step_err)
         ref = runs["f64"][0]
         scale = ref.abs().max().item()
-        out["precision"] = {"steps": steps}
-        for name, (u, ms) in runs.items():
-            out["precision"][name] = {"ms_per_step": ms,
-                                      "rel_linf_vs_f64": (u - ref).abs().max().item() / scale}
+        out["precision"] = {"steps": steps, "weights": "F16 (F64 for the f64 run)",
+                            "error": "relative L-inf against the FP64 run; per step: one step from the same "
+                                     "rounded u^n against the FP64 step of it"}
+        for name, (u, ms, e1) in runs.items():
+            out["precision"][name] = {"ms_per_step": ms, "rel_linf_vs_f64": (u - ref).abs().max().item() / scale,
+                                      "per_step_rel_linf": e1}
         return out
     finally:
         ab.adlbr_stencils_destroy(h16)

@@ -104,17 +104,18 @@ __global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled(int nx, int ny, int 
                                      blockIdx.y * TY, blockIdx.z * TZ, smem);
 }
 
-template <int TX, int TY, int TZ, bool F16W>
+// FP32 or 16-bit u on a non-periodic grid: the window arrives by one TMA copy.
+template <typename UT, int TX, int TY, int TZ, bool F16W>
 __global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled_tma(int nx, int ny, int nz, int bc, float scale,
                                                                 const char4 *__restrict__ offs,
                                                                 const void *__restrict__ wbase, adlbr_dtype wt,
-                                                                const float *__restrict__ u, float *__restrict__ acc,
+                                                                const UT *__restrict__ u, float *__restrict__ acc,
                                                                 const int *__restrict__ skip,
                                                                 const __grid_constant__ CUtensorMap map, int *err) {
     extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
-    op::tile3d<float, TX, TY, TZ, F16W, true>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
-                                              blockIdx.y * TY, blockIdx.z * TZ, smem, &map, err);
+    op::tile3d<UT, TX, TY, TZ, F16W, true>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
+                                           blockIdx.y * TY, blockIdx.z * TZ, smem, &map, err);
 }
 
 template <typename UT, typename AT = typename UTraits<UT>::acc>
@@ -137,6 +138,26 @@ __global__ void finalize_kernel(int64_t N, UT *__restrict__ u,
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     u[i] = from_acc<UT>(to_acc(u[i]) - acc[i]);
+}
+
+// u <- round(u - acc) for 16-bit u, eight values per thread (one 16-byte
+// load and store of u, two of acc)
+template <typename UT>
+__global__ void finalize_h8_kernel(int64_t N8, uint4 *__restrict__ u, const float4 *__restrict__ acc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N8) return;
+    uint4 v = u[i];
+    const float4 a0 = acc[2 * i], a1 = acc[2 * i + 1];
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    uint32_t *w = reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const UT lo = from_acc<UT>(to_acc(*reinterpret_cast<const UT *>(&w[k])) - a[2 * k]);
+        const UT hi = from_acc<UT>(to_acc(*(reinterpret_cast<const UT *>(&w[k]) + 1)) - a[2 * k + 1]);
+        w[k] = (uint32_t)*reinterpret_cast<const uint16_t *>(&lo) | (uint32_t)*reinterpret_cast<const uint16_t *>(&hi)
+                                                                         << 16;
+    }
+    u[i] = v;
 }
 
 __global__ void finalize_f32x4_kernel(int64_t N4, float4 *__restrict__ u, const float4 *__restrict__ acc) {
@@ -287,17 +308,25 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
         dim3 grid(blocks_for(s->n[0], TX), blocks_for(s->n[1], TY), blocks_for(s->n[2], TZ));
         using B3 = op::Block3<TX, TY, TZ>;
         CUtensorMap map;
-        if (std::is_same<UT, float>::value && s->bc != ADLBR_PERIODIC &&
-            tma::encode_3d_f32(&map, reinterpret_cast<const float *>(u), (int)s->n[0], (int)s->n[1],
-                               (int)s->n[2], B3::WX, B3::WY, B3::WZ)) {
+        constexpr bool F32U = std::is_same<UT, float>::value;
+        // 16-bit u: the window's staging box follows the two FP32 windows
+        constexpr size_t smem_tma = smem + (F32U ? 0 : B3::STAGE16 * 2);
+        static_assert(smem_tma <= 48 * 1024, "default shared-memory limit");
+        const bool tma_ok =
+            s->bc != ADLBR_PERIODIC &&
+            (F32U ? tma::encode_3d_f32(&map, reinterpret_cast<const float *>(u), (int)s->n[0], (int)s->n[1],
+                                       (int)s->n[2], B3::WX, B3::WY, B3::WZ)
+                  : tma::encode_3d_u16(&map, u, (int)s->n[0], (int)s->n[1], (int)s->n[2], B3::H16, B3::WY,
+                                       B3::WZ));
+        if (tma_ok) {
             if (s->w_t == ADLBR_F16)
-                apply3d_tiled_tma<TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
+                apply3d_tiled_tma<UT, TX, TY, TZ, true><<<grid, TX * TY, smem_tma, st>>>(
                     (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs, s->w,
-                    s->w_t, reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+                    s->w_t, u, acc, skip, map, s->err);
             else
-                apply3d_tiled_tma<TX, TY, TZ, false><<<grid, TX * TY, smem, st>>>(
+                apply3d_tiled_tma<UT, TX, TY, TZ, false><<<grid, TX * TY, smem_tma, st>>>(
                     (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs, s->w,
-                    s->w_t, reinterpret_cast<const float *>(u), acc, skip, map, s->err);
+                    s->w_t, u, acc, skip, map, s->err);
         } else if (s->w_t == ADLBR_F16)
             apply3d_tiled<UT, TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
                 (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
@@ -370,12 +399,20 @@ adlbr_status launch_finalize(const adlbr_stencils *s, void *u, void *acc, adlbr_
             finalize_kernel<float><<<blocks, threads, 0, st>>>(s->N, (float *)u, (float *)acc);
         break;
     case ADLBR_F16:
-        finalize_kernel<__half><<<blocks, threads, 0, st>>>(s->N, (__half *)u, (float *)acc);
+    case ADLBR_BF16: {
+        const bool v8 = s->N % 8 == 0 && ((uintptr_t)u % 16) == 0 && ((uintptr_t)acc % 16) == 0;
+        if (v8 && u_t == ADLBR_F16)
+            finalize_h8_kernel<__half><<<blocks_for(s->N / 8, threads), threads, 0, st>>>(s->N / 8, (uint4 *)u,
+                                                                                          (const float4 *)acc);
+        else if (v8)
+            finalize_h8_kernel<__nv_bfloat16><<<blocks_for(s->N / 8, threads), threads, 0, st>>>(
+                s->N / 8, (uint4 *)u, (const float4 *)acc);
+        else if (u_t == ADLBR_F16)
+            finalize_kernel<__half><<<blocks, threads, 0, st>>>(s->N, (__half *)u, (float *)acc);
+        else
+            finalize_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(s->N, (__nv_bfloat16 *)u, (float *)acc);
         break;
-    case ADLBR_BF16:
-        finalize_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(s->N, (__nv_bfloat16 *)u,
-                                                                   (float *)acc);
-        break;
+    }
     default: return fail(ADLBR_E_ARG, "bad u dtype %d", (int)u_t);
     }
     ADLBR_CUDA(cudaGetLastError());

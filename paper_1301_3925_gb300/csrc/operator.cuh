@@ -259,6 +259,8 @@ struct Block3 {
     static constexpr int PX = WX;                     // row pitch
     static constexpr int PY = WY * PX;                // plane pitch
     static constexpr int CELLS = WZ * PY;
+    static constexpr int H16 = TX + 16;                // staged 16-bit box width (x0 - 8 .. x0 + TX + 8)
+    static constexpr int STAGE16 = H16 * WY * WZ;      // its cells (2 bytes each)
 };
 
 // Weights of 3D point z (8 lanes: six F16 weights and the meta lane) times
@@ -275,8 +277,10 @@ __device__ __forceinline__ void weights6_f16_scaled(const void *wbase, int64_t z
 
 // acc += scale A u over the block at (x0, y0, z0); all TX * TY threads of
 // the CTA call it.  smem: 2 * Block3::CELLS floats, 16-byte aligned (128 for
-// TMA).  TMA: as in tile2d, the window (a WX x WY x WZ box) arrives by one
-// bulk tensor copy on non-periodic FP32 grids.
+// TMA), plus Block3::STAGE16 halves for 16-bit u with TMA.  TMA: as in
+// tile2d, the window (a WX x WY x WZ box) arrives by one bulk tensor copy on
+// non-periodic grids: FP32 u straight into the window; 16-bit u (x from
+// x0 - 8, a 16-byte boundary) into a staging box that is then widened.
 template <typename UT, int TX, int TY, int TZ, bool F16W, bool TMA = false>
 __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float scale,
                                        const char4 *__restrict__ offs, const void *__restrict__ wbase,
@@ -295,13 +299,23 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
     const int64_t nxy = (int64_t)nx * ny;
     constexpr int Q = PX / 4;   // float4s per window row
     if constexpr (TMA) {
-        static_assert(std::is_same<UT, float>::value, "TMA windows are FP32");
+        // FP32 u lands in the window itself; 16-bit u lands in a staging box
+        // after the two windows (x from x0 - 8, a 16-byte boundary, H16 wide)
+        // and is widened below
+        constexpr bool F32U = std::is_same<UT, float>::value;
+        static_assert(F32U || sizeof(UT) == 2, "TMA windows: FP32 or 16-bit u");
+        uint16_t *st16 = reinterpret_cast<uint16_t *>(smem + 2 * B::CELLS);
         __shared__ uint64_t bar;
         if (threadIdx.x == 0) tma::bar_init(&bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma::bar_expect_tx(&bar, B::CELLS * sizeof(float));
-            tma::load_3d(uw, map, wx0, y0 - H3, z0 - H3, &bar);
+            if constexpr (F32U) {
+                tma::bar_expect_tx(&bar, B::CELLS * sizeof(float));
+                tma::load_3d(uw, map, wx0, y0 - H3, z0 - H3, &bar);
+            } else {
+                tma::bar_expect_tx(&bar, B::H16 * WY * WZ * 2);
+                tma::load_3d(st16, map, x0 - 8, y0 - H3, z0 - H3, &bar);
+            }
         }
         for (int c4 = threadIdx.x; c4 < B::CELLS / 4; c4 += NT)
             *reinterpret_cast<float4 *>(&aw[c4 * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -317,6 +331,15 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
             }
             __syncthreads();
             return;
+        }
+        if constexpr (!F32U) {
+            // widen: window column wx is staged column wx + 8 - XL
+            for (int c = threadIdx.x; c < B::CELLS; c += NT) {
+                const int row = c / PX, wx = c - row * PX;
+                const uint16_t h = st16[row * B::H16 + wx + 8 - XL];
+                uw[c] = to_acc(*reinterpret_cast<const UT *>(&h));
+            }
+            __syncthreads();
         }
     } else {
     // stage u (4 cells per step), zero the accumulator

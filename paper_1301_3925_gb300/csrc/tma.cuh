@@ -107,6 +107,22 @@ inline bool encode_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, i
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Host: a 3D map of 16-bit elements (F16 / BF16 bits, zero fill) over an
+// nx x ny x nz array with a box of bx x by x bz elements; the row pitch and
+// every copy's x must be 16-byte multiples: nx % 8 == 0, x % 8 == 0.
+inline bool encode_3d_u16(CUtensorMap *map, const void *base, int nx, int ny, int nz, int bx, int by, int bz) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
+    if (!encode) return false;
+    if (((uintptr_t)base & 15) || (nx % 8) || bx > 256 || by > 256 || bz > 256 || (bx * 2) % 16) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 2, (cuuint64_t)nx * ny * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Host: a 2D FP32 tensor map over a row-major nx x ny array with a box of
 // bx x by elements (zero fill out of bounds).  False when the driver entry
 // point is unavailable or the layout is not encodable (the caller then uses

@@ -228,3 +228,35 @@ def test_periodic_fourier_modes_are_eigenvectors(dim):
     sig = sum(4 * ow[0, j] * (1 - np.cos(sum(xi_xyz[c] * e[j, c] for c in range(dim))))
               for j in range(e.shape[0]))
     assert np.abs(Au - sig * u).max() <= 1e-12 * max(1.0, sig)
+
+
+@pytest.mark.parametrize("u_name", ["float16", "bfloat16"])
+@pytest.mark.parametrize("nx", [32, 28])
+def test_apply3d_half_vectors(u_name, nx):
+    """3D operator on 16-bit u (F16 weights), against the oracle fed the same
+    rounded u: nx = 32 takes the TMA window (16-bit staging box widened in
+    shared memory), nx = 28 the plain loads; then two explicit steps (the
+    vectorised 16-bit finalize) against the oracle's."""
+    t = torch()
+    shape = (20, 24, nx)
+    D = synth.needle_field3d(32, seed=6, kappa=20.0)[:, :20, :24, :nx]
+    h, seen, _ = build(D, shape, t.float32, ab.F16)
+    ud = getattr(t, u_name)
+    try:
+        oo, ow = export(h, shape, ab.F16)
+        u = dev(synth.u_uniform(shape, 2).ravel(), ud)
+        useen = u.double().cpu().numpy().reshape(shape)
+        Au, _ = _gpu_apply(h, useen, ud)
+        dt = oracle.dt_limit(shape, oracle.NEUMANN, oo, ow)
+        scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.dtype_code(ud)), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(h, u, scratch, ab.dtype_code(ud), dt, 1)
+        t.cuda.synchronize()
+        u1 = u.double().cpu().numpy().reshape(shape)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    ref = oracle.apply(shape, ab.NEUMANN, oo, ow, useen)
+    assert np.abs(Au - ref).max() <= 1e-5 * np.abs(ref).max()
+    # one step, rounded once to the storage type (half an ulp of 1: 2^-11 / 2^-8)
+    step = oracle.step_explicit(shape, oracle.NEUMANN, oo, ow, useen, dt, 1)
+    tol = {"float16": 2.0 ** -11, "bfloat16": 2.0 ** -8}[u_name]
+    assert np.abs(u1 - step).max() <= tol * np.abs(step).max() + 1e-6
