@@ -60,9 +60,9 @@ def fp32_peak_tops():
 # DRAM bytes (read + write) of one launch at 4096^2, from an ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum, one launch each,
 # second warm-up step of this benchmark's CED step)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.183e6 + 140.391e6, "build2d_kernel": 201.348e6 + 229.138e6,
+TRAFFIC_4096 = {"ced_fused_kernel": 67.183e6 + 139.635e6, "build2d_kernel": 201.390e6 + 225.449e6,
                 # operator + finalize
-                "explicit_step": 402.735e6 + 51.184e6 + 134.225e6 + 21.878e6}
+                "explicit_step": 402.755e6 + 48.226e6 + 134.241e6 + 18.940e6}
 
 
 def parse():
@@ -84,6 +84,9 @@ def parse():
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
     p.add_argument("--profile-unet", action="store_true",
                    help="only run four tensor-core U-Net forwards at 512^2 (for ncu launch lists)")
+    p.add_argument("--profile-gather", action="store_true",
+                   help="only run three gather-form applications of the operator on 2048^2 CED stencils "
+                        "(for ncu)")
     p.add_argument("--profile-fcg", action="store_true",
                    help="only run two 40-iteration flexible-CG solves with the U-Net preconditioner "
                         "at 2048^2 (for ncu launch lists)")
@@ -379,6 +382,32 @@ def profile_fcg():
         pc.close()
         ab.adlbr_stencils_destroy(h)
     print(json.dumps({"profile_fcg": {"solves": [str(o) for o in out]}}))
+    return 0
+
+
+def profile_gather():
+    """Three applications of the operator in its gather form on the CED
+    stencils of a 2048^2 crop of the fingerprint image (F16 weights, FP32 u);
+    the first builds the table (profiling entry)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    n = 2048
+    g = ab.grid((n, n))
+    u = torch.from_numpy(synth.fingerprint(N_SIDE, SEED)[:n, :n].astype(np.float32).ravel()).cuda()
+    scratch = torch.empty(ab.adlbr_ced_scratch_bytes(g), dtype=torch.uint8, device="cuda")
+    h = ab.adlbr_ced_stencils(None, g, u, scratch, *(CED[k] for k in ("sigma", "rho", "alpha", "C")), ab.F16)
+    Au = torch.empty_like(u)
+    try:
+        ab.adlbr_stencils_set_operator(h, ab.OP_GATHER)
+        for _ in range(3):
+            ab.adlbr_apply(h, u, Au, ab.F32)
+        torch.cuda.synchronize()
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    print(json.dumps({"profile_gather": {"Au_abs_max": float(Au.abs().max())}}))
     return 0
 
 
@@ -805,6 +834,8 @@ def main():
         return profile_unet()
     if args.profile_fcg:
         return profile_fcg()
+    if args.profile_gather:
+        return profile_gather()
 
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
@@ -909,7 +940,21 @@ def main():
     apply_gbs = 24 * N / (apply_ms * 1e-3) / 1e9
     apply_sub = {"ms": apply_ms, "gpts": N / (apply_ms * 1e-3) / 1e9, "gbs": apply_gbs,
                  "frac_hbm": apply_gbs / peak, "bytes_per_point": 24,
-                 "stencils": "CED kappa <= 100 (4096^2 fingerprint)"}
+                 "stencils": "CED kappa <= 100 (4096^2 fingerprint)", "form": "scatter (the default)"}
+    # the same applications in the gather form (its table built first, not timed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ab.adlbr_stencils_set_operator(h, ab.OP_GATHER)
+    ab.adlbr_apply(h, u, Au, ab.F32)
+    torch.cuda.synchronize()
+    table_ms = (time.perf_counter() - t0) * 1e3
+    g_ms = time_ms(lambda: ab.adlbr_apply(h, u, Au, ab.F32), 20, stream)
+    ab.adlbr_stencils_set_operator(h, ab.OP_AUTO)
+    apply_sub["gather_form"] = {"ms": g_ms, "gpts": N / (g_ms * 1e-3) / 1e9,
+                                "frac_hbm_24B": 24 * N / (g_ms * 1e-3) / 1e9 / peak,
+                                "first_call_with_table_build_ms": table_ms,
+                                "note": "deterministic gather form, measured beside the scatter; slower, "
+                                        "so not the default"}
 
     # End to end through the C ABI with host buffers: every step copies its
     # input image from pinned host memory and reads its result back.  As a
