@@ -50,7 +50,9 @@ typedef enum {
     ADLBR_E_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     ADLBR_E_CUDA = 7,          /* a CUDA runtime call failed */
     ADLBR_E_RANGE = 8,         /* an offset does not fit the stencil format */
-    ADLBR_E_INTERNAL = 9
+    ADLBR_E_INTERNAL = 9       /* library invariant broken; in the bounds-
+                                  checked build (see adlbr_version), also an
+                                  index or stencil-radius check that failed */
 } adlbr_status;
 
 typedef enum { ADLBR_F64 = 0, ADLBR_F32 = 1, ADLBR_F16 = 2, ADLBR_BF16 = 3 } adlbr_dtype;
@@ -67,7 +69,20 @@ typedef struct {
 
 typedef struct adlbr_stencils adlbr_stencils; /* opaque, library-owned */
 
-/* Library version string. */
+/* Library version string.  The bounds-checked build of the library
+ * (libadlbr_checked.so, compiled with -DADLBR_BOUNDS_CHECK) says
+ * "bounds-checked" here.  In that build every data-dependent index of the
+ * operator kernels (neighbour positions in the shared window and in the
+ * grid, entries of the gather table) is checked before the access: an index
+ * out of range is skipped and recorded in the handle's sticky status, and
+ * the 2D AD-LBR build checks every offset of non-zero weight against the
+ * bound |e| <= max(kappa(D), sqrt 2) (Sec. 4.1, Remark "Stencil
+ * radius"; the sqrt 2 covers nearly isotropic tensors).  A failed check
+ * is returned as ADLBR_E_INTERNAL by adlbr_stencils_check, or by
+ * adlbr_stencils_destroy when no check collected it.  Results are otherwise
+ * those of the normal build.  Each compute entry point and stage (tensor,
+ * build, operator) also opens an NVTX range named after it, in both
+ * builds. */
 const char *adlbr_version(void);
 
 /* Message describing the last non-OK status returned on the calling thread. */
@@ -136,8 +151,9 @@ adlbr_status adlbr_stencils_scheme(const adlbr_stencils *s, int *scheme);
 
 /* Synchronises `stream`, returns the handle's sticky build status
  * (ADLBR_OK, ADLBR_E_NONFINITE, ADLBR_E_NOT_SPD, ADLBR_E_RANGE,
- * ADLBR_E_NOT_CONVERGED, or ADLBR_E_TIMEOUT when an operator kernel on this
- * handle gave up a bounded wait for a tile copy) and clears it. */
+ * ADLBR_E_NOT_CONVERGED, ADLBR_E_TIMEOUT when an operator kernel on this
+ * handle gave up a bounded wait for a tile copy, or ADLBR_E_INTERNAL when a
+ * check of the bounds-checked build failed) and clears it. */
 adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream);
 
 /* Grid of a handle. */
@@ -158,6 +174,9 @@ adlbr_status adlbr_stencils_grid(const adlbr_stencils *s, adlbr_grid *g);
 adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void *w,
                                    cudaStream_t stream);
 
+/* Frees the handle (waits for the device).  Returns ADLBR_OK, or in the
+ * bounds-checked build ADLBR_E_INTERNAL when a check failed that no
+ * adlbr_stencils_check collected (the handle is freed all the same). */
 adlbr_status adlbr_stencils_destroy(adlbr_stencils *s);
 
 /*

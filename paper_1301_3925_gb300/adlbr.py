@@ -10,7 +10,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libadlbr.so")
+# ADLBR_BOUNDS_CHECK=1 selects the bounds-checked build of the library
+CHECKED = os.environ.get("ADLBR_BOUNDS_CHECK", "") == "1"
+LIB_PATH = os.path.join(_HERE, "libadlbr_checked.so" if CHECKED else "libadlbr.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 NEUMANN, PERIODIC = 0, 1
@@ -51,7 +53,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libadlbr.so is not built (run paper_1301_3925_gb300.build)")
+            raise ImportError("%s is not built (run paper_1301_3925_gb300.build%s)"
+                              % (os.path.basename(LIB_PATH), " --checked" if CHECKED else ""))
         L = ctypes.CDLL(LIB_PATH)
         sigs = {
             "adlbr_version": (ctypes.c_char_p, []),

@@ -1,10 +1,15 @@
 """Builds libadlbr.so in-tree for sm_103a.
 
-    python -m paper_1301_3925_gb300.build [--force]
+    python -m paper_1301_3925_gb300.build [--force] [--checked]
 
 Every ``csrc/*.cu`` is compiled to an object in parallel with
 ``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
 ``paper_1301_3925_gb300/libadlbr.so``.  Objects go to ``_build/`` (git-ignored).
+
+``--checked`` builds the bounds-checked variant instead
+(``-DADLBR_BOUNDS_CHECK``, objects in ``_build/checked/``,
+``paper_1301_3925_gb300/libadlbr_checked.so``); the binding loads it when
+the environment sets ``ADLBR_BOUNDS_CHECK=1``.
 """
 import concurrent.futures as cf
 import glob
@@ -18,6 +23,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libadlbr.so")
+LIB_CHECKED = os.path.join(HERE, "libadlbr_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,9 +32,10 @@ def _nvcc():
     return cand
 
 
-def _flags():
+def _flags(checked=False):
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-I", os.path.join(ROOT, "include"), "-Xptxas", "-warn-spills"]
+                   "-I", os.path.join(ROOT, "include"), "-Xptxas", "-warn-spills"] + \
+        (["-DADLBR_BOUNDS_CHECK"] if checked else [])
 
 
 def _deps():
@@ -42,10 +49,10 @@ def _stale(obj, src):
     return any(os.path.getmtime(p) > t for p in [src] + _deps())
 
 
-def _compile(src):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, checked=False):
+    obj = os.path.join(BUILD, "checked" if checked else "", os.path.basename(src)[:-3] + ".o")
     if _stale(obj, src):
-        cmd = [_nvcc()] + _flags() + ["-c", src, "-o", obj]
+        cmd = [_nvcc()] + _flags(checked) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -54,23 +61,25 @@ def _compile(src):
     return obj
 
 
-def build(force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, checked: bool = False) -> str:
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if force:
-        for o in glob.glob(os.path.join(BUILD, "*.o")):
+        for o in glob.glob(os.path.join(bdir, "*.o")):
             os.remove(o)
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(_compile, srcs))
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp.%d" % os.getpid()
-        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        objs = list(ex.map(lambda src: _compile(src, checked), srcs))
+    if force or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp.%d" % os.getpid()
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, checked="--checked" in sys.argv))

@@ -104,7 +104,9 @@ using namespace adlbr;
 
 extern "C" {
 
-const char *adlbr_version(void) { return "adlbr-gb300 0.1 (sm_103a)"; }
+const char *adlbr_version(void) {
+    return kBoundsCheck ? "adlbr-gb300 0.1 (sm_103a, bounds-checked)" : "adlbr-gb300 0.1 (sm_103a)";
+}
 
 const char *adlbr_last_error(void) { return g_msg; }
 
@@ -118,6 +120,7 @@ adlbr_status adlbr_build_stencils(const adlbr_grid *g, const void *D, adlbr_dtyp
 adlbr_status adlbr_build_stencils_scheme(const adlbr_grid *g, const void *D, adlbr_dtype D_t,
                                          adlbr_dtype w_t, int scheme, adlbr_stencils **out,
                                          cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_build_stencils_scheme");
     if (!out || !D) return fail(ADLBR_E_ARG, "null argument");
     if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "invalid grid");
     if (D_t != ADLBR_F32 && D_t != ADLBR_F64) return fail(ADLBR_E_ARG, "D must be F32 or F64");
@@ -150,6 +153,8 @@ adlbr_status adlbr_stencils_check(adlbr_stencils *s, cudaStream_t stream) {
     if (bits & ERRBIT_RANGE) return fail(ADLBR_E_RANGE, "stencil offset out of storage range");
     if (bits & ERRBIT_NOT_CONVERGED) return fail(ADLBR_E_NOT_CONVERGED, "reduction did not converge");
     if (bits & ERRBIT_TIMEOUT) return fail(ADLBR_E_TIMEOUT, "a device-side wait for a tile copy gave up");
+    if (bits & ERRBIT_BOUNDS)
+        return fail(ADLBR_E_INTERNAL, "an index or stencil-radius check of the bounds-checked build failed");
     return ADLBR_OK;
 }
 
@@ -173,6 +178,7 @@ adlbr_status adlbr_stencils_grid(const adlbr_stencils *s, adlbr_grid *g) {
 
 adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void *w,
                                    cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_stencils_export");
     if (adlbr_status st = check_handle(s)) return st;
     if (!offs || !w) return fail(ADLBR_E_ARG, "null output");
     return launch_export(s, offs, w, stream);
@@ -180,6 +186,11 @@ adlbr_status adlbr_stencils_export(const adlbr_stencils *s, int16_t *offs, void 
 
 adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
     if (!s) return ADLBR_OK;
+    // bounds-checked build: a failed check that no adlbr_stencils_check
+    // collected is reported here (the copy waits for the device)
+    int bits = 0;
+    if (kBoundsCheck && s->err && cudaMemcpy(&bits, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        bits = 0;
     if (s->offs) cudaFree(s->offs);
     if (s->offs3) cudaFree(s->offs3);
     if (s->w) cudaFree(s->w);
@@ -189,11 +200,14 @@ adlbr_status adlbr_stencils_destroy(adlbr_stencils *s) {
     if (s->ws_nn) cudaFree(s->ws_nn);
     pull_free(s);
     delete s;
+    if (bits & ERRBIT_BOUNDS)
+        return fail(ADLBR_E_INTERNAL, "an index or stencil-radius check of the bounds-checked build failed");
     return ADLBR_OK;
 }
 
 adlbr_status adlbr_apply(const adlbr_stencils *s, const void *u, void *Au, adlbr_dtype u_t,
                          cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_apply");
     if (adlbr_status st = check_handle(s)) return st;
     if (!u || !Au) return fail(ADLBR_E_ARG, "null vector");
     if (u == Au) return fail(ADLBR_E_ARG, "Au must not alias u");
@@ -224,6 +238,7 @@ size_t adlbr_step_scratch_bytes(const adlbr_stencils *s, adlbr_dtype u_t) {
 
 adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch, adlbr_dtype u_t,
                                  double dt, int nsteps, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_step_explicit");
     if (adlbr_status st = check_handle(s)) return st;
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
     if (nsteps < 0 || !(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt / nsteps");
@@ -260,6 +275,7 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
 adlbr_status adlbr_step_implicit(adlbr_stencils *s, const void *rhs, void *x, double dt,
                                  double rtol, int maxit, int precond, const void *nn,
                                  int *iters_out, double *relres_out, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_step_implicit");
     if (adlbr_status st = check_handle(s)) return st;
     if (!rhs || !x) return fail(ADLBR_E_ARG, "null vector");
     if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
@@ -277,6 +293,7 @@ adlbr_status adlbr_nn_training_pairs(adlbr_stencils *s, const float *rhs, double
                                      int maxit, int every, int max_pairs,
                                      const adlbr_nn_precond *nn, float *feats, float *targets,
                                      float *xbuf, int *n_pairs, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_nn_training_pairs");
     if (adlbr_status st = check_handle(s)) return st;
     if (!rhs || !feats || !targets || !xbuf) return fail(ADLBR_E_ARG, "null buffer");
     if (!(dt >= 0.0) || !(rtol > 0.0) || maxit < 1) return fail(ADLBR_E_ARG, "bad dt / rtol / maxit");
@@ -286,6 +303,7 @@ adlbr_status adlbr_nn_training_pairs(adlbr_stencils *s, const float *rhs, double
 
 adlbr_status adlbr_nn_precondition(adlbr_stencils *s, const adlbr_nn_precond *nn, double dt,
                                    const float *r, float *z, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_nn_precondition");
     if (adlbr_status st = check_handle(s)) return st;
     if (!r || !z) return fail(ADLBR_E_ARG, "null buffer");
     return nn_apply(s, nn, dt, r, z, stream);
@@ -319,6 +337,7 @@ size_t adlbr_ced_scratch_bytes(const adlbr_grid *g) {
 adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, double sigma,
                               double rho, double alpha, double C, void *scratch,
                               cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_ced_tensor");
     if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !D || !scratch) return fail(ADLBR_E_ARG, "null buffer");
     if (g->dim == 3)
@@ -330,6 +349,7 @@ adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, dou
 adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const float *u,
                                 void *scratch, double sigma, double rho, double alpha, double C,
                                 adlbr_dtype w_t, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_ced_stencils");
     if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
     if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");
@@ -350,6 +370,7 @@ adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const f
 adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, void *scratch,
                             double sigma, double rho, double alpha, double C, double dt,
                             int nsteps, adlbr_dtype w_t, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_ced_step");
     if (!s) return fail(ADLBR_E_ARG, "null handle pointer");
     if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "CED needs a valid 2D or 3D grid");
     if (!u || !scratch) return fail(ADLBR_E_ARG, "null buffer");

@@ -44,11 +44,11 @@ __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, floa
                                                     const short2 *__restrict__ offs3,
                                                     const void *__restrict__ wbase, adlbr_dtype wt,
                                                     const UT *__restrict__ u, float *__restrict__ acc,
-                                                    const int *__restrict__ skip) {
+                                                    const int *__restrict__ skip, int *err) {
     extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
     op::tile2d<UT, TW, TH, NT, WX, F16W>(nx, ny, bc, scale, offs, offs3, wbase, wt, u, acc, blockIdx.x * TW,
-                                         blockIdx.y * TH, smem);
+                                         blockIdx.y * TH, smem, nullptr, err);
 }
 
 // ---- direct scatter (FP64 in 2D) ----------------------------------------
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, A
                                                        const short4 *__restrict__ offs,
                                                        const short2 *__restrict__ offs3,
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
-                                                       const UT *__restrict__ u, AT *__restrict__ Au) {
+                                                       const UT *__restrict__ u, AT *__restrict__ Au, int *err) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= nx) return;
@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) apply2d_scatter(int nx, int ny, int bc, A
                 continue;
             }
             const int64_t zn = (int64_t)yn * nx + xn;
+            if (!in_bounds(zn, (int64_t)nx * ny, err)) continue;
             const AT flux = wk * (uz - to_acc(u[zn]));
             acc += flux;
             red_add(Au + zn, -flux);
@@ -97,11 +98,11 @@ __global__ void __launch_bounds__(TX * TY, 5) apply3d_tiled(int nx, int ny, int 
                                                          const char4 *__restrict__ offs,
                                                          const void *__restrict__ wbase, adlbr_dtype wt,
                                                          const UT *__restrict__ u, float *__restrict__ acc,
-                                                         const int *__restrict__ skip) {
+                                                         const int *__restrict__ skip, int *err) {
     extern __shared__ __align__(128) float smem[];
     if (skip && *skip) return;
     op::tile3d<UT, TX, TY, TZ, F16W>(nx, ny, nz, bc, scale, offs, wbase, wt, u, acc, blockIdx.x * TX,
-                                     blockIdx.y * TY, blockIdx.z * TZ, smem);
+                                     blockIdx.y * TY, blockIdx.z * TZ, smem, nullptr, err);
 }
 
 // FP32 or 16-bit u on a non-periodic grid: the window arrives by one TMA copy.
@@ -122,10 +123,10 @@ template <typename UT, typename AT = typename UTraits<UT>::acc>
 __global__ void __launch_bounds__(128) apply3d_scatter(int nx, int ny, int nz, int bc, AT scale,
                                                        const char4 *__restrict__ offs,
                                                        const void *__restrict__ wbase, adlbr_dtype wt,
-                                                       const UT *__restrict__ u, AT *__restrict__ Au) {
+                                                       const UT *__restrict__ u, AT *__restrict__ Au, int *err) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
-    op::point3d<UT, AT>(nx, ny, nz, bc, scale, offs, wbase, wt, u, Au, x, blockIdx.y, blockIdx.z);
+    op::point3d<UT, AT>(nx, ny, nz, bc, scale, offs, wbase, wt, u, Au, x, blockIdx.y, blockIdx.z, err);
 }
 
 // u <- u - acc   (acc holds dt A u).  The accumulator is cleared by a
@@ -289,17 +290,17 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
             } else if (s->w_t == ADLBR_F16)
                 apply2d_tiled<UT, TW, TH, NT, WX, true><<<grid, NT, smem, st>>>(
                     (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w,
-                    s->w_t, u, acc, skip);
+                    s->w_t, u, acc, skip, s->err);
             else
                 apply2d_tiled<UT, TW, TH, NT, WX, false><<<grid, NT, smem, st>>>(
                     (int)s->n[0], (int)s->n[1], s->bc, (float)scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w,
-                    s->w_t, u, acc, skip);
+                    s->w_t, u, acc, skip, s->err);
         } else {
             const int threads = 256;
             dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
             apply2d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], s->bc, (AT)scale,
                                                           (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t, u,
-                                                          acc);
+                                                          acc, s->err);
         }
     } else if constexpr (sizeof(AT) == 4) {
         constexpr int TX = 32, TY = 8, TZ = 4;   // 30 KB window, 5 CTAs per SM
@@ -330,17 +331,17 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
         } else if (s->w_t == ADLBR_F16)
             apply3d_tiled<UT, TX, TY, TZ, true><<<grid, TX * TY, smem, st>>>(
                 (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
-                s->w, s->w_t, u, acc, skip);
+                s->w, s->w_t, u, acc, skip, s->err);
         else
             apply3d_tiled<UT, TX, TY, TZ, false><<<grid, TX * TY, smem, st>>>(
                 (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, (float)scale, (const char4 *)s->offs,
-                s->w, s->w_t, u, acc, skip);
+                s->w, s->w_t, u, acc, skip, s->err);
     } else {
         const int threads = 128;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);
         apply3d_scatter<UT><<<grid, threads, 0, st>>>((int)s->n[0], (int)s->n[1], (int)s->n[2],
                                                       s->bc, (AT)scale, (const char4 *)s->offs, s->w,
-                                                      s->w_t, u, acc);
+                                                      s->w_t, u, acc, s->err);
     }
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
@@ -348,6 +349,7 @@ static adlbr_status accumulate_t(const adlbr_stencils *s, const UT *u, typename 
 
 adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,
                                double scale, const int *skip, cudaStream_t st) {
+    ADLBR_NVTX("operator");
     switch (u_t) {
     case ADLBR_F64: return accumulate_t<double>(s, (const double *)u, (double *)acc, scale, skip, st);
     case ADLBR_F32: return accumulate_t<float>(s, (const float *)u, (float *)acc, scale, skip, st);
@@ -364,13 +366,14 @@ adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, doub
         const int threads = 256;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1]);
         apply2d_scatter<float, double><<<grid, threads, 0, st>>>(
-            (int)s->n[0], (int)s->n[1], s->bc, scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t, u, acc);
+            (int)s->n[0], (int)s->n[1], s->bc, scale, (const short4 *)s->offs, (const short2 *)s->offs3, s->w, s->w_t, u, acc,
+            s->err);
     } else {
         const int threads = 128;
         dim3 grid(blocks_for(s->n[0], threads), (unsigned)s->n[1], (unsigned)s->n[2]);
         apply3d_scatter<float, double><<<grid, threads, 0, st>>>(
             (int)s->n[0], (int)s->n[1], (int)s->n[2], s->bc, scale, (const char4 *)s->offs, s->w,
-            s->w_t, u, acc);
+            s->w_t, u, acc, s->err);
     }
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;

@@ -364,6 +364,7 @@ adlbr_status adlbr_batch_create(int n_items, adlbr_stencils *const *s, float *co
 }
 
 adlbr_status adlbr_batch_step(adlbr_batch *b, int nsteps, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_batch_step");
     if (!b) return fail(ADLBR_E_ARG, "null batch");
     if (nsteps < 0) return fail(ADLBR_E_ARG, "bad nsteps");
     int dev = -1;

@@ -21,41 +21,41 @@ namespace adlbr {
 
 namespace {
 
+// Integer vector held in floats: every coordinate (at most 4 * 127 during
+// the reduction) and every product below is an exact integer in FP32, so
+// the vector arithmetic is exact and needs no integer-to-float conversions.
 struct V3 {
-    int x, y, z;
+    float x, y, z;
 };
 
 __device__ __forceinline__ V3 add(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ V3 sub(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 neg(V3 a) { return V3{-a.x, -a.y, -a.z}; }
-__device__ __forceinline__ V3 mul(int k, V3 a) { return V3{k * a.x, k * a.y, k * a.z}; }
-__device__ __forceinline__ int amax(V3 a) { return max(abs(a.x), max(abs(a.y), abs(a.z))); }
+// a - k b (exact: integers below 2^24)
+__device__ __forceinline__ V3 sub_mul(V3 a, float k, V3 b) {
+    return V3{__fmaf_rn(-k, b.x, a.x), __fmaf_rn(-k, b.y, a.y), __fmaf_rn(-k, b.z, a.z)};
+}
+__device__ __forceinline__ float amax(V3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
 
 // d = (xx, yy, zz, xy, xz, yz)
 __device__ __forceinline__ float g3(const float (&d)[6], V3 u, V3 v) {
-    float ux = u.x, uy = u.y, uz = u.z, vx = v.x, vy = v.y, vz = v.z;
+    const float ux = u.x, uy = u.y, uz = u.z, vx = v.x, vy = v.y, vz = v.z;
     return d[0] * ux * vx + d[1] * uy * vy + d[2] * uz * vz + d[3] * (ux * vy + uy * vx) +
            d[4] * (ux * vz + uz * vx) + d[5] * (uy * vz + uz * vy);
 }
 
+// <u, D v> = sum_k n_k D_k with the integers n_k as exact floats
+// (|n_k| <= 2 * 127^2)
 template <typename T>
-__device__ __forceinline__ void terms3(const T (&D)[6], V3 u, V3 v, T (&x)[6], int (&n)[6]) {
+__device__ __forceinline__ void terms3(const T (&D)[6], V3 u, V3 v, T (&x)[6], float (&n)[6]) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) x[k] = D[k];
-    n[0] = u.x * v.x;
-    n[1] = u.y * v.y;
-    n[2] = u.z * v.z;
-    n[3] = u.x * v.y + u.y * v.x;
-    n[4] = u.x * v.z + u.z * v.x;
-    n[5] = u.y * v.z + u.z * v.y;
-}
-
-template <typename T>
-__device__ __forceinline__ int sgnD(const T (&D)[6], V3 u, V3 v) {
-    T x[6];
-    int n[6];
-    terms3(D, u, v, x, n);
-    return exact_sign<6>(x, n);
+    n[0] = __fmul_rn(u.x, v.x);
+    n[1] = __fmul_rn(u.y, v.y);
+    n[2] = __fmul_rn(u.z, v.z);
+    n[3] = __fmaf_rn(u.x, v.y, __fmul_rn(u.y, v.x));
+    n[4] = __fmaf_rn(u.x, v.z, __fmul_rn(u.z, v.x));
+    n[5] = __fmaf_rn(u.y, v.z, __fmul_rn(u.z, v.y));
 }
 
 __device__ __forceinline__ bool finite(float v) { return isfinite(v); }
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     // products with the third vector linearly), and recomputed from the
     // vectors once per round.  The result is certified exactly below, so the
     // rounding of these values can only cost repair steps.
-    V3 b[3] = {V3{1, 0, 0}, V3{0, 1, 0}, V3{0, 0, 1}};
+    V3 b[3] = {V3{1.f, 0.f, 0.f}, V3{0.f, 1.f, 0.f}, V3{0.f, 0.f, 1.f}};
     for (int it = 0; it < 24; ++it) {
         float G[3][3];
         gram3(d, b, G);
@@ -169,8 +169,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
             if (!(gff > 0.f)) break;
             float r = rintf(gef / gff);
             r = fminf(fmaxf(r, -256.f), 256.f);
-            const int ri = (int)r;
-            const V3 nf = sub(e, mul(ri, f));
+            const V3 nf = sub_mul(e, r, f);
             const float gnn = fmaf(-r, fmaf(-r, gff, 2.f * gef), gee);
             const float gfn = fmaf(-r, gff, gef);
             const float hn = fmaf(-r, hf, he);
@@ -178,7 +177,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
             e = f;
             f = nf;
             gee = gff, gef = gfn, gff = gnn, he = hf, hf = hn;
-            if (amax(f) > 4 * kMaxCoord) break;
+            if (amax(f) > (float)(4 * kMaxCoord)) break;
             if (!shorter) break;
         }
         b[0] = e;
@@ -191,24 +190,24 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
         float y0 = (G11 * r0 - G01 * r1) / det, y1 = (G00 * r1 - G01 * r0) / det;
         y0 = fminf(fmaxf(y0, -512.f), 512.f);
         y1 = fminf(fmaxf(y1, -512.f), 512.f);
-        const int f0 = (int)floorf(y0), f1 = (int)floorf(y1);
-        int bk0 = 0, bk1 = 0;
+        const float f0 = floorf(y0), f1 = floorf(y1);
+        float bk0 = 0.f, bk1 = 0.f;
         float bestn = 3.4e38f;
 #pragma unroll
         for (int k0 = -1; k0 <= 2; ++k0)
 #pragma unroll
             for (int k1 = -1; k1 <= 2; ++k1) {
-                const float a0 = (float)(f0 + k0), a1 = (float)(f1 + k1);
+                const float a0 = f0 + (float)k0, a1 = f1 + (float)k1;
                 const float nt = fmaf(a0, fmaf(a0, G00, fmaf(2.f * a1, G01, -2.f * r0)),
                                       fmaf(a1, fmaf(a1, G11, -2.f * r1), G22));
                 if (nt < bestn) {
                     bestn = nt;
-                    bk0 = f0 + k0;
-                    bk1 = f1 + k1;
+                    bk0 = a0;
+                    bk1 = a1;
                 }
             }
-        b[2] = sub(b[2], add(mul(bk0, b[0]), mul(bk1, b[1])));
-        if (amax(b[2]) > 4 * kMaxCoord) break;
+        b[2] = sub_mul(sub_mul(b[2], bk0, b[0]), bk1, b[1]);
+        if (amax(b[2]) > (float)(4 * kMaxCoord)) break;
         if (bestn >= G11) break;
     }
 
@@ -258,15 +257,15 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     for (int fix = 0; fix < 256; ++fix) {
         range = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) range |= amax(e[k]) > kMaxCoord;
+        for (int k = 0; k < 4; ++k) range |= amax(e[k]) > (float)kMaxCoord;
         if (range) break;
         int bad = -1;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             T x[6];
-            int n[6];
+            float n[6];
             terms3(D, e[PI[q]], e[PJ[q]], x, n);
-            sg[q] = sign_value<6>(x, n, val[q]);
+            sg[q] = sign_value_nf<6>(x, n, val[q]);
             if (sg[q] > 0 && bad < 0) bad = q;
         }
         if (bad < 0) {
@@ -297,13 +296,14 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
     }
 #pragma unroll
     for (int k = 1; k < 4; ++k)
-        o[k - 1] = make_char4((signed char)e[k].x, (signed char)e[k].y, (signed char)e[k].z, 0);
+        o[k - 1] = make_char4((signed char)(int)e[k].x, (signed char)(int)e[k].y, (signed char)(int)e[k].z, 0);
     store_weights<6>(wbase, wt, i, wz, zmask);
 }
 
 }  // namespace
 
 adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st) {
+    ADLBR_NVTX("build");
     const int threads = 128;
     unsigned blocks = blocks_for(s->N, threads);
     if (D_t == ADLBR_F32)

@@ -470,6 +470,7 @@ size_t ced_tensor_scratch_bytes(int64_t N) { return (size_t)N * sizeof(float) * 
 
 adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double sigma, double rho,
                                double alpha, double C, void *scratch, cudaStream_t st) {
+    ADLBR_NVTX("tensor");
     if (adlbr_status e = check_params(sigma, rho, alpha, C)) return e;
     const int rs = radius_of(sigma), rr = radius_of(rho);
     if (ced_path() != 1 && fused_ok(nx, ny, rr, rs))

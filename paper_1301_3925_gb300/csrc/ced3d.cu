@@ -144,6 +144,7 @@ size_t ced_tensor3d_scratch_bytes(int64_t N) { return (size_t)N * sizeof(float) 
 
 adlbr_status launch_ced_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
                                  double alpha, double C, void *scratch, cudaStream_t st) {
+    ADLBR_NVTX("tensor");
     if (!(sigma > 0) || !(rho > 0) || !(alpha > 0 && alpha <= 1) || !(C >= 0))
         return fail(ADLBR_E_ARG, "bad CED parameters");
     const int rs = radius_of(sigma), rr = radius_of(rho);

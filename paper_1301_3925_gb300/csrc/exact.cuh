@@ -195,6 +195,46 @@ __device__ __forceinline__ int sign_value(const double (&x)[K], const int (&n)[K
     return exact_sign_slow_f64<K>(x, n);
 }
 
+// sign_value with the integer multipliers given as floats (integers below
+// 2^24, so exactly representable): the fast path has no integer-to-float
+// conversion, and the first product starts the float-float sum (s = p,
+// c = its fma error) instead of being added to zero.  Same filter and the
+// same exact fallback as sign_value.
+template <int K>
+__device__ __forceinline__ int sign_value_nf(const float (&x)[K], const float (&nf)[K], FF &val) {
+    float s = __fmul_rn(nf[0], x[0]);
+    float c = __fmaf_rn(nf[0], x[0], -s);
+    float A = fabsf(s);
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        const float p = __fmul_rn(nf[k], x[k]);
+        const float pe = __fmaf_rn(nf[k], x[k], -p);
+        const float t = __fadd_rn(s, p);
+        const float bv = __fsub_rn(t, s);
+        const float av = __fsub_rn(t, bv);
+        const float err = __fadd_rn(__fsub_rn(s, av), __fsub_rn(p, bv));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, pe));
+        A = __fadd_rn(A, fabsf(p));
+    }
+    val = FF{s, c};
+    if (A == 0.f) return 0;
+    const float v = __fadd_rn(s, c);
+    const float bound = __fmaf_rn(A, (float)(8 * K * K) * 0x1p-48f, 0x1p-126f);
+    if (fabsf(v) > bound) return v > 0.f ? 1 : -1;
+    int n[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) n[k] = (int)nf[k];
+    return exact_sign_slow_f32<K>(x, n);
+}
+template <int K>
+__device__ __forceinline__ int sign_value_nf(const double (&x)[K], const float (&nf)[K], double &val) {
+    int n[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) n[k] = (int)nf[k];
+    return sign_value<K>(x, n, val);
+}
+
 // Dispatch on the input type.
 template <int K>
 __device__ __forceinline__ int exact_sign(const float (&x)[K], const int (&n)[K]) {

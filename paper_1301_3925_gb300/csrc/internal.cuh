@@ -9,6 +9,8 @@
 #include <cstdarg>
 #include <cstdio>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/adlbr.h"
 
 namespace adlbr {
@@ -30,7 +32,35 @@ enum : int {
     ERRBIT_RANGE = 1 << 2,
     ERRBIT_NOT_CONVERGED = 1 << 3,
     ERRBIT_TIMEOUT = 1 << 4,   // a bounded device-side wait gave up
+    ERRBIT_BOUNDS = 1 << 5,    // a check of the bounds-checked build failed
 };
+
+// Index guard.  In the bounds-checked build (-DADLBR_BOUNDS_CHECK) an index
+// outside [0, n) records ERRBIT_BOUNDS in *err (when err is given) and the
+// caller skips the access; in the normal build the guard is the constant
+// true and costs nothing.
+#ifdef ADLBR_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int *err) {
+    if ((uint64_t)i < (uint64_t)n) return true;
+    if (err) atomicOr(err, ERRBIT_BOUNDS);
+    return false;
+}
+#else
+constexpr bool kBoundsCheck = false;
+__device__ __forceinline__ constexpr bool in_bounds(int64_t, int64_t, int *) { return true; }
+#endif
+
+// NVTX range over one entry point or stage (tensor, build, operator, solve),
+// for timelines and for ncu's --nvtx filters.  Header-only NVTX v3: without
+// an attached tool a push and a pop cost a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define ADLBR_NVTX(name) ::adlbr::NvtxRange adlbr_nvtx_range_(name)
 
 }  // namespace adlbr
 

@@ -193,6 +193,7 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
                         if ((unsigned)xn >= (unsigned)nx || (unsigned)yn >= (unsigned)ny) continue;
                     }
                     const int zn = zw + sg * d;
+                    if (!in_bounds(zn, WH * P, err)) continue;
                     const float f = wi * (uz - uw[zn]);
                     own += f;
                     atomicAdd(&aw[zn], -f);
@@ -208,6 +209,7 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
                         continue;
                     }
                     const int64_t zn = (int64_t)yn * nx + xn;
+                    if (!in_bounds(zn, (int64_t)nx * ny, err)) continue;
                     const float f = wi * (uz - to_acc(u[zn]));
                     own += f;
                     red_add(acc + zn, -f);
@@ -412,6 +414,7 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
                                 continue;
                         }
                         const int zn = zw + sg * d;
+                        if (!in_bounds(zn, B::CELLS, err)) continue;
                         const float f = wq * (uz - uw[zn]);
                         own += f;
                         atomicAdd(&aw[zn], -f);
@@ -429,6 +432,7 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
                             continue;
                         }
                         const int64_t zz = zn * nxy + (int64_t)yn * nx + xn;
+                        if (!in_bounds(zz, nxy * nz, err)) continue;
                         const float f = wq * (uz - to_acc(u[zz]));
                         own += f;
                         red_add(acc + zz, -f);
@@ -476,7 +480,8 @@ __device__ __forceinline__ void tile3d(int nx, int ny, int nz, int bc, float sca
 template <typename UT, typename AT>
 __device__ __forceinline__ void point3d(int nx, int ny, int nz, int bc, AT scale, const char4 *__restrict__ offs,
                                         const void *__restrict__ wbase, adlbr_dtype wt,
-                                        const UT *__restrict__ u, AT *__restrict__ Au, int x, int y, int zc) {
+                                        const UT *__restrict__ u, AT *__restrict__ Au, int x, int y, int zc,
+                                        int *err = nullptr) {
     const int64_t z = ((int64_t)zc * ny + y) * nx + x;
     const char4 b[3] = {offs[3 * z], offs[3 * z + 1], offs[3 * z + 2]};
     int c[6][3];
@@ -500,6 +505,7 @@ __device__ __forceinline__ void point3d(int nx, int ny, int nz, int bc, AT scale
                 continue;
             }
             const int64_t zz = ((int64_t)zn * ny + yn) * nx + xn;
+            if (!in_bounds(zz, (int64_t)nx * ny * nz, err)) continue;
             const AT flux = wq * (uz - to_acc(u[zz]));
             acc += flux;
             red_add(Au + zz, -flux);

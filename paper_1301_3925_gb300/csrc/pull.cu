@@ -313,7 +313,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 template <typename UT>
 __device__ __forceinline__ float long_term(int nx, int ny, int periodic, const uint4 *__restrict__ recw,
                                            const uint2 *__restrict__ reco, const UT *__restrict__ u, int xt, int y,
-                                           float uz, bool extra, uint32_t v, int q) {
+                                           float uz, bool extra, uint32_t v, int q, int *err) {
     int dx, dy;
     float c;
     const int64_t z = (int64_t)y * nx + xt;
@@ -344,7 +344,9 @@ __device__ __forceinline__ float long_term(int nx, int ny, int periodic, const u
         xn = wrapc(xn, nx);
         yn = wrapc(yn, ny);
     }
-    return c * (uz - to_acc(u[(int64_t)yn * nx + xn]));
+    const int64_t zn = (int64_t)yn * nx + xn;
+    if (!in_bounds(zn, (int64_t)nx * ny, err)) return 0.f;
+    return c * (uz - to_acc(u[zn]));
 }
 
 // out[z] = a u(z) + b (A u)(z) over a TW x TH tile per CTA.
@@ -360,7 +362,7 @@ template <typename UT, typename OT, int TW, int TH, int NT, bool TMA>
 __global__ void __launch_bounds__(NT, 4) pull2d_kernel(int nx, int ny, int periodic, const uint4 *__restrict__ recw,
                                                        const uint2 *__restrict__ reco,
                                                        const uint32_t *__restrict__ ext,
-                                                       const uint32_t *__restrict__ seg, int nseg_x,
+                                                       const uint32_t *__restrict__ seg, int nseg_x, int64_t n_ext,
                                                        const UT *__restrict__ u, OT *__restrict__ out, float a, float b,
                                                        const int *__restrict__ skip,
                                                        const __grid_constant__ CUtensorMap umap, int *err) {
@@ -503,29 +505,33 @@ __global__ void __launch_bounds__(NT, 4) pull2d_kernel(int nx, int ny, int perio
                         ((unsigned)(x + dx) >= (unsigned)nx || (unsigned)(y + dy) >= (unsigned)ny))
                         continue;   // the pair leaves the grid (Neumann)
                     if (shrt) {
+                        if (!in_bounds(zw + (s ? -lin : lin), PT::CELLS, err)) continue;
                         acc = __fmaf_rn(w[i] + rho[q], uz - uw[zw + (s ? -lin : lin)], acc);
                     } else {
                         const int slot = atomicAdd(&lq_n[warp], 1);
                         if (slot < LQ)
                             myq[slot] = make_uint2((uint32_t)k << 26 | (uint32_t)lane << 21 | (uint32_t)q, 0u);
                         else
-                            acc += long_term<UT>(nx, ny, periodic, recw, reco, u, x, y, uz, false, 0u, q);
+                            acc += long_term<UT>(nx, ny, periodic, recw, reco, u, x, y, uz, false, 0u, q, err);
                     }
                 }
             }
             const uint32_t eg = sb + pre - cnt;
             const int es = row_off[ly] + (int)(eg - row_a[ly]);
             for (unsigned t = 0; t < cnt; ++t) {
+                if (!(from_l2 ? in_bounds((int64_t)eg + t, n_ext, err) : in_bounds(es + (int)t, PT::EXT_CAP, err)))
+                    continue;
                 const uint32_t v = from_l2 ? ext[eg + t] : xs[es + t];
                 const int dx = (int)(int8_t)(v & 0xffu), dy = (int)(int8_t)((v >> 8) & 0xffu);
                 if (abs(dx) <= H && abs(dy) <= H) {
+                    if (!in_bounds(zw + dy * WW + dx, PT::CELLS, err)) continue;
                     acc = __fmaf_rn(hf(v >> 16), uz - uw[zw + dy * WW + dx], acc);
                 } else {
                     const int slot = atomicAdd(&lq_n[warp], 1);
                     if (slot < LQ)
                         myq[slot] = make_uint2(0x80000000u | (uint32_t)k << 26 | (uint32_t)lane << 21, v);
                     else
-                        acc += long_term<UT>(nx, ny, periodic, recw, reco, u, x, y, uz, true, v, 0);
+                        acc += long_term<UT>(nx, ny, periodic, recw, reco, u, x, y, uz, true, v, 0, err);
                 }
             }
             acc *= pow2f((int)(int8_t)((ro.x >> 16) & 0xffu));   // the point's weight scale
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(NT, 4) pull2d_kernel(int nx, int ny, int perio
         const int ly = ry + k * RG, y = y0 + ly, xt = x0 + cx0 + tl;
         const float uz = uw[(ly + H) * WW + cx0 + tl + H];
         const float t = long_term<UT>(nx, ny, periodic, recw, reco, u, xt, y, uz, (item.x >> 31) != 0, item.y,
-                                      (int)(item.x & 7u));
+                                      (int)(item.x & 7u), err);
         const int sz = (int)(int8_t)((reco[(int64_t)y * nx + xt].x >> 16) & 0xffu);
         atomicAdd(&myacc[k * 32 + tl], t * pow2f(sz));
     }
@@ -578,8 +584,8 @@ adlbr_status launch_pull_u(const adlbr_stencils *s, const UT *u, OT *out, float 
             ADLBR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k<<<grid, PNT, smem, st>>>(nx, ny, 0, T.recw, T.reco, T.ext, T.seg, T.nseg_x, u, out, a, b, skip, um,
-                                   s->err);
+        k<<<grid, PNT, smem, st>>>(nx, ny, 0, T.recw, T.reco, T.ext, T.seg, T.nseg_x, T.cap + 4, u, out, a, b,
+                                   skip, um, s->err);
     } else {
         auto k = pull2d_kernel<UT, OT, PTW, PTH, PNT, false>;
         static bool attr = false;
@@ -587,8 +593,8 @@ adlbr_status launch_pull_u(const adlbr_stencils *s, const UT *u, OT *out, float 
             ADLBR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr = true;
         }
-        k<<<grid, PNT, smem, st>>>(nx, ny, s->bc == ADLBR_PERIODIC, T.recw, T.reco, T.ext, T.seg, T.nseg_x, u, out,
-                                   a, b, skip, um, s->err);
+        k<<<grid, PNT, smem, st>>>(nx, ny, s->bc == ADLBR_PERIODIC, T.recw, T.reco, T.ext, T.seg, T.nseg_x,
+                                   T.cap + 4, u, out, a, b, skip, um, s->err);
     }
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
@@ -674,6 +680,7 @@ bool pull_ready(const adlbr_stencils *s) { return s->pull && s->pull->built && s
 // out = a u + b A u through the gather form (pull_ready(s) must hold).
 adlbr_status launch_pull(const adlbr_stencils *s, const void *u, adlbr_dtype u_t, void *out, adlbr_dtype out_t,
                          double a, double b, const int *skip, cudaStream_t st) {
+    ADLBR_NVTX("operator");
     const float fa = (float)a, fb = (float)b;
     if (out_t == ADLBR_F32) {
         switch (u_t) {

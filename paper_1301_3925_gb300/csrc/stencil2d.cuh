@@ -25,27 +25,22 @@
 namespace adlbr {
 namespace s2d {
 
+// Integer vector held in floats: coordinates up to kMaxCoord, so every
+// coordinate and every product below is an exact integer in FP32.
 struct V2 {
-    int x, y;
+    float x, y;
 };
 
-// <u, adj(D) v> = c ux vx - b (ux vy + uy vx) + a uy vy, terms (x_k, n_k).
+// <u, adj(D) v> = c ux vx - b (ux vy + uy vx) + a uy vy, terms (x_k, n_k)
+// with the integers n_k as exact floats (|n_k| <= 2 * 2047^2 < 2^24).
 template <typename T>
-__device__ __forceinline__ void terms2(T a, T b, T c, V2 u, V2 v, T (&x)[3], int (&n)[3]) {
+__device__ __forceinline__ void terms2(T a, T b, T c, V2 u, V2 v, T (&x)[3], float (&n)[3]) {
     x[0] = c;
-    n[0] = u.x * v.x;
+    n[0] = __fmul_rn(u.x, v.x);
     x[1] = b;
-    n[1] = -(u.x * v.y + u.y * v.x);
+    n[1] = -__fmaf_rn(u.x, v.y, __fmul_rn(u.y, v.x));
     x[2] = a;
-    n[2] = u.y * v.y;
-}
-
-template <typename T>
-__device__ __forceinline__ int sgnS(T a, T b, T c, V2 u, V2 v) {
-    T x[3];
-    int n[3];
-    terms2(a, b, c, u, v, x, n);
-    return exact_sign<3>(x, n);
+    n[2] = __fmul_rn(u.y, v.y);
 }
 
 static __device__ __noinline__ bool det_positive_slow(float a, float b, float c) {
@@ -154,7 +149,7 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
     }
     // (ii) orientation of f
     if (gef > 0.f) fx = -fx, fy = -fy;
-    V2 e{(int)ex, (int)ey}, f{(int)fx, (int)fy};
+    V2 e{ex, ey}, f{fx, fy};
 
     // (iii) superbase, certified and repaired with exact signs
     V2 v[3] = {e, f, V2{-e.x - f.x, -e.y - f.y}};
@@ -166,9 +161,9 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             T x[3];
-            int n[3];
+            float n[3];
             terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
-            sg[k] = sign_value<3>(x, n, val[k]);
+            sg[k] = sign_value_nf<3>(x, n, val[k]);
             if (sg[k] > 0 && bad < 0) bad = k;
         }
         if (bad < 0) {
@@ -180,11 +175,11 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
         V2 vj = v[j], vl = v[l];
         v[j] = V2{-vj.x, -vj.y};
         v[bad] = V2{vj.x - vl.x, vj.y - vl.y};
-        if (abs(v[bad].x) > kMaxCoord || abs(v[bad].y) > kMaxCoord) break;
+        if (fabsf(v[bad].x) > (float)kMaxCoord || fabsf(v[bad].y) > (float)kMaxCoord) break;
     }
     bool range = false;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) range |= abs(v[k].x) > kMaxCoord || abs(v[k].y) > kMaxCoord;
+    for (int k = 0; k < 3; ++k) range |= fabsf(v[k].x) > (float)kMaxCoord || fabsf(v[k].y) > (float)kMaxCoord;
     if (!ok || range) {
         offs[i] = make_short4(0, 0, 0, 0);
         store_weights<3>(wbase, wt, i, wz, 7u);
@@ -203,7 +198,23 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
             wz[k] = wmax0(neg_half(val[k]));
         }
     }
-    offs[i] = make_short4((short)v[0].x, (short)v[0].y, (short)v[1].x, (short)v[1].y);
+    if constexpr (kBoundsCheck) {
+        // Remark "Stencil radius": every offset of non-zero weight has
+        // |e| <= max(kappa(D), sqrt 2), i.e. |e|^2 det(D) <= max(2 det(D),
+        // lambda_max(D)^2) (FP64, with a relative margin for the rounding of
+        // det and lambda_max).  Below kappa = sqrt 2 the third superbase
+        // vector, of length sqrt 2, can carry a small positive weight.
+        const double da = (double)a, db = (double)b, dc = (double)c;
+        const double det = fma(da, dc, -db * db);
+        const double lmax = 0.5 * (da + dc + sqrt((da - dc) * (da - dc) + 4.0 * db * db));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double r2 = (double)v[k].x * v[k].x + (double)v[k].y * v[k].y;
+            if (!(zmask >> k & 1u) && r2 * det > fmax(2.0 * det, lmax * lmax) * (1.0 + 1e-6))
+                atomicOr(err, ERRBIT_BOUNDS);
+        }
+    }
+    offs[i] = make_short4((short)(int)v[0].x, (short)(int)v[0].y, (short)(int)v[1].x, (short)(int)v[1].y);
     store_weights<3>(wbase, wt, i, wz, zmask);
 }
 

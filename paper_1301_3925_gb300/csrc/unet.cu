@@ -703,12 +703,14 @@ int64_t adlbr_unet_num_params(const adlbr_unet *n) { return unet_num_params(n); 
 
 adlbr_status adlbr_unet_forward(adlbr_unet *n, const float *params, const float *x, float *y,
                                 cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_unet_forward");
     if (!n || !params || !x || !y) return fail(ADLBR_E_ARG, "null argument");
     return unet_forward(n, params, x, y, stream);
 }
 
 adlbr_status adlbr_unet_backward(adlbr_unet *n, const float *params, const float *gy,
                                  float *gparams, float *gx, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_unet_backward");
     if (!n || !params || !gy || !gparams) return fail(ADLBR_E_ARG, "null argument");
     if (!n->x) return fail(ADLBR_E_ARG, "backward before any forward");
     if (n->fwd_tc) return fail(ADLBR_E_ARG, "backward after a tensor-core (BF16) forward");

@@ -97,6 +97,26 @@ def test_fig_radius_kappa10():
     assert rad.max() > printed - 0.1              # the bound is attained (sqrt 26)
 
 
+def test_radius_bound_random_tensors():
+    """Remark "Stencil radius": the offsets of non-zero weight satisfy
+    |e| <= kappa(D) once kappa(D) >= sqrt 2; below, the third superbase
+    vector (length sqrt 2) can carry a small positive weight, so the bound
+    read for every tensor is max(kappa, sqrt 2).  Random orientations and
+    scales, kappa log-uniform in [1, 1000]."""
+    rng = np.random.default_rng(11)
+    n = 100000
+    th = rng.uniform(0, np.pi, n)
+    kap = np.exp(rng.uniform(0, np.log(1000.0), n))
+    D = synth.D_from_angle(th, kap) * rng.uniform(0.1, 10.0, n)
+    offs, w, st, _ = oracle.build2d(*D)
+    assert np.all(st == 0)
+    r = np.sqrt((offs.astype(float) ** 2).sum(-1)).max(axis=1)   # zero-weight offsets are (0, 0)
+    assert np.all(r <= np.maximum(kap, np.sqrt(2.0)) * (1 + 1e-9))
+    big = kap >= np.sqrt(2.0)
+    assert np.all(r[big] <= kap[big] * (1 + 1e-9))
+    assert np.any(r[~big] > kap[~big])   # the sqrt 2 case does occur
+
+
 def test_fig_eigen_tensor_exact_weights():
     """D = [[19/2, 6], [6, 4]] (Fig. Eigen).  Worked by hand: the superbase
     (1,1), (-3,-2), (2,1) has det 1 and, with S = adj D = [[4,-6],[-6,19/2]],
