@@ -80,6 +80,9 @@ def parse():
     p.add_argument("--no-spectral", action="store_true", help="skip the periodic spectral study")
     p.add_argument("--no-ann", action="store_true", help="skip the A-NN comparison scheme")
     p.add_argument("--precision-steps", type=int, default=100)
+    p.add_argument("--cpu-configs", action="store_true",
+                   help="only time the oracle on samples of the other workloads (64^2 FP64 build and steps, "
+                        "3D steps, CG iterations, batch items), one thread and every host core")
     p.add_argument("--profile-cg", action="store_true",
                    help="only run three plain-CG implicit solves at 2048^2 (for ncu launch lists)")
     p.add_argument("--profile-unet", action="store_true",
@@ -468,7 +471,7 @@ def batch_measurement(peak, steps=20):
                 "ms_per_step": ms, "gpts": points / (ms * 1e-3) / 1e9, "gbs": gbs,
                 "frac_hbm": gbs / peak, "bytes_per_point": {"2d": 24, "3d": 36},
                 "looped_ms_per_step": ms_loop, "speedup_vs_looped": ms_loop / ms,
-                "kernel_launches_per_step": {"batched": 2, "looped": 2 * len(hs)}}
+                "kernel_launches_per_step": {"batched": 3, "looped": 2 * len(hs)}}
     finally:
         for h in hs:
             ab.adlbr_stencils_destroy(h)
@@ -723,6 +726,130 @@ def _oracle_worker(args):
     return steps * side * side, time.perf_counter() - t0
 
 
+CPU_CONFIG_UNITS = {1: "runs/s (build + 10 explicit steps, 64^2 FP64 spiral)",
+                    3: "Gpts/s (3D explicit steps, 64^3 crop of the needle field)",
+                    4: "G point-iterations/s (plain CG on a 512^2 kappa <= 50 field, dt = 200 / max A_zz)",
+                    5: "Gpts/s (explicit steps on a 256^2 image and a 64^3 volume of the batch's kind)"}
+
+
+def _cfg_runner(cfg, k):
+    """The oracle's work unit for workload `cfg` in process k: returns a
+    function that runs it once and gives the units it processed."""
+    import oracle
+    import synth
+    if cfg == 1:
+        D = synth.spiral_field(64, 10.0).reshape(3, -1)
+        u0 = synth.u_uniform((64, 64), k)
+
+        def run():
+            offs, w, st, _ = oracle.build2d(*D)
+            dt = oracle.dt_limit((64, 64), oracle.NEUMANN, offs, w)
+            oracle.step_explicit((64, 64), oracle.NEUMANN, offs, w, u0, dt, 10)
+            return 1
+        return run
+    if cfg == 3:
+        n = 64
+        offs, w, st, _ = oracle.build3d(synth.needle_field3d(n, 2 + k, kappa=20.0).reshape(6, -1))
+        dt = oracle.dt_limit((n, n, n), oracle.NEUMANN, offs, w)
+        state = {"u": synth.u_uniform((n, n, n), k)}
+
+        def run():
+            state["u"] = oracle.step_explicit((n, n, n), oracle.NEUMANN, offs, w, state["u"], dt, 1)
+            return n ** 3
+        return run
+    if cfg == 4:
+        n = 512
+        offs, w, st, _ = oracle.build2d(*synth.smooth_field2d(n, n, 3 + k, 1.0, 50.0, 16).reshape(3, -1))
+        dt = 200.0 / oracle.diag((n, n), oracle.NEUMANN, offs, w).max()
+        b = synth.u_uniform((n, n), 3 + k)
+
+        def run():
+            _, it, _ = oracle.cg((n, n), oracle.NEUMANN, offs, w, b, b, dt, 1e-6, 20)
+            return n * n * it
+        return run
+    # cfg == 5
+    D2 = synth.smooth_field2d(256, 256, 100 + k, 1.0, 50.0, 16).reshape(3, -1)
+    o2, w2, _, _ = oracle.build2d(*D2)
+    d2 = oracle.dt_limit((256, 256), oracle.NEUMANN, o2, w2)
+    o3, w3, _, _ = oracle.build3d(synth.needle_field3d(64, 200 + k, kappa=20.0).reshape(6, -1))
+    d3 = oracle.dt_limit((64, 64, 64), oracle.NEUMANN, o3, w3)
+    st = {"a": synth.u_uniform((256, 256), k), "b": synth.u_uniform((64, 64, 64), k)}
+
+    def run():
+        st["a"] = oracle.step_explicit((256, 256), oracle.NEUMANN, o2, w2, st["a"], d2, 1)
+        st["b"] = oracle.step_explicit((64, 64, 64), oracle.NEUMANN, o3, w3, st["b"], d3, 1)
+        return 256 * 256 + 64 ** 3
+    return run
+
+
+def _cfg_worker(args):
+    """Runs workload `cfg`'s oracle unit for about `budget_s` seconds after one
+    untimed run; returns (units, seconds)."""
+    cfg, k, budget_s = args
+    run = _cfg_runner(cfg, k)
+    run()
+    t0 = time.perf_counter()
+    units = 0
+    while time.perf_counter() - t0 < budget_s:
+        units += run()
+    return units, time.perf_counter() - t0
+
+
+def cpu_configs(budget_s=4.0):
+    """The oracle on samples of the other workloads, one thread and then every
+    host core (one spawned process per core, each on its own sample)."""
+    import multiprocessing as mp
+    model, ncpu = cpu_model()
+    ctx = mp.get_context("spawn")
+    out = {}
+    for cfg in (1, 3, 4, 5):
+        u1, t1 = _cfg_worker((cfg, 0, budget_s))
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_cfg_worker, [(cfg, k, budget_s) for k in range(ncpu)])
+        allv = sum(r[0] for r in res) / max(r[1] for r in res)
+        scale = 1.0 if cfg == 1 else 1e-9
+        out[str(cfg)] = {"unit": CPU_CONFIG_UNITS[cfg], "single_thread": u1 / t1 * scale,
+                         "all_core": allv * scale, "cores": ncpu}
+    print(json.dumps({"cpu_configs": out, "cpu_model": model, "nproc": ncpu, "kind": "oracle",
+                      "budget_s_per_leg": budget_s}))
+    return 0
+
+
+def small_measurement():
+    """The 64^2 FP64 spiral workload on the GPU: stencil build (FP64 D and
+    weights), the explicit limit dt = 1 / max A_zz (read back to the host) and
+    10 explicit steps, per run."""
+    import torch
+    import synth
+    from paper_1301_3925_gb300 import adlbr as ab
+    n = 64
+    D = torch.from_numpy(synth.spiral_field(n, 10.0).reshape(3, -1)).cuda()
+    u0 = torch.from_numpy(synth.u_uniform((n, n), 0).ravel()).cuda()
+    u = u0.clone()
+    g = ab.grid((n, n))
+    h = ab.adlbr_build_stencils(g, D, ab.F64, ab.F64)
+    scratch = torch.empty(ab.adlbr_step_scratch_bytes(h, ab.F64), dtype=torch.uint8, device="cuda")
+    try:
+        def run():
+            ab.adlbr_build_stencils(g, D, ab.F64, ab.F64, out=h)
+            dt = 1.0 / ab.adlbr_stencils_max_diag(h)
+            u.copy_(u0)
+            ab.adlbr_step_explicit(h, u, scratch, ab.F64, dt, 10)
+        for _ in range(5):
+            run()
+        torch.cuda.synchronize()
+        reps = 200
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            run()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    return {"grid": [n, n], "ms_per_run": ms, "runs_per_s": 1e3 / ms,
+            "run": "build (FP64) + max A_zz to the host + 10 explicit steps, wall clock per run"}
+
+
 def cpu_baseline(budget_s=12.0, side=1024, all_side=512, all_budget_s=10.0):
     """Times the oracle as it stands on crops of the workload: one thread on a
     side^2 crop, then every host core at once, each core a separate process
@@ -827,6 +954,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_configs:
+        import __graft_entry__
+        __graft_entry__.build()
+        return cpu_configs()
     import torch
     if args.profile_cg:
         return profile_cg()
@@ -1017,6 +1148,7 @@ def main():
         ced3d["plain_cg"] = {k: plain[k] for k in ("ms_per_step", "implicit_ms", "cg_iters_mean", "rms_to_clean")}
     spectral_study = None if args.no_spectral or rank != 0 else spectral_measurement()
     ann_study = None if args.no_ann or rank != 0 else ann_measurement(peak)
+    small = small_measurement() if rank == 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -1043,7 +1175,7 @@ def main():
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
                                   "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
                 "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch,
-                "ced3d": ced3d, "spectral": spectral_study, "ann": ann_study}
+                "ced3d": ced3d, "spectral": spectral_study, "ann": ann_study, "small_64_fp64": small}
         print(json.dumps(line))
     ab.adlbr_stencils_destroy(h)
     if ws > 1:

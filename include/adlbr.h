@@ -506,8 +506,9 @@ typedef struct adlbr_batch adlbr_batch; /* opaque: items, work list, accumulator
  * With autotune != 0 it times the accumulate kernel of every candidate tile
  * shape on this batch (u is not modified) and keeps the fastest, else the
  * first candidate (64 x 32 tiles, 32 x 8 x 4 blocks).  One step (accumulator
- * reset, one persistent accumulate kernel over all tiles of all items with
- * dynamic tile hand-out, one finalize kernel) is recorded as a CUDA graph.
+ * reset, one persistent accumulate kernel over the 2D tiles of all images and
+ * one over the 3D blocks of all volumes, each with dynamic tile hand-out, one
+ * finalize kernel) is recorded as a CUDA graph.
  * Synchronises the stream.  The handles' stencils must not be rebuilt with a
  * different shape while the batch lives (rebuilding in place is fine).
  */
