@@ -795,15 +795,26 @@ def _cfg_worker(args):
     return units, time.perf_counter() - t0
 
 
+def one_thread_env():
+    """Pins the numerical libraries of processes spawned from here on to one
+    thread each (numpy's BLAS would otherwise start a thread per core in
+    every process of an all-core leg)."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
 def cpu_configs(budget_s=4.0):
-    """The oracle on samples of the other workloads, one thread and then every
-    host core (one spawned process per core, each on its own sample)."""
+    """The oracle on samples of the other workloads, one thread (one spawned
+    process) and then every host core (one spawned process per core, each on
+    its own sample), every process with single-threaded numerical libraries."""
     import multiprocessing as mp
     model, ncpu = cpu_model()
+    one_thread_env()
     ctx = mp.get_context("spawn")
     out = {}
     for cfg in (1, 3, 4, 5):
-        u1, t1 = _cfg_worker((cfg, 0, budget_s))
+        with ctx.Pool(1) as pool:
+            u1, t1 = pool.map(_cfg_worker, [(cfg, 0, budget_s)])[0]
         with ctx.Pool(ncpu) as pool:
             res = pool.map(_cfg_worker, [(cfg, k, budget_s) for k in range(ncpu)])
         allv = sum(r[0] for r in res) / max(r[1] for r in res)
@@ -871,6 +882,7 @@ def cpu_baseline(budget_s=12.0, side=1024, all_side=512, all_budget_s=10.0):
     dt = time.perf_counter() - t0
     one = steps * side * side / dt / 1e9
     model, ncpu = cpu_model()
+    one_thread_env()
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(ncpu) as pool:

@@ -64,6 +64,39 @@ def test_batch_matches_single_grid_steps(autotune):
             ab.adlbr_stencils_destroy(h)
 
 
+@pytest.mark.parametrize("kind", [2, 3])
+def test_batch_of_one_kind(kind):
+    """Images only or volumes only: the other accumulate kernel has no tiles
+    and is not launched; every tuned shape still matches the single-grid
+    step."""
+    t = torch()
+    hs, us, dts, _ = _setup()
+    keep = [k for k, it in enumerate(ITEMS) if len(it[0]) == kind]
+    for k in range(len(ITEMS)):
+        if k not in keep:
+            ab.adlbr_stencils_destroy(hs[k])
+    hs, us, dts = [hs[k] for k in keep], [us[k] for k in keep], [dts[k] for k in keep]
+    ref = [u.clone() for u in us]
+    b = None
+    try:
+        for h, u, d in zip(hs, ref, dts):
+            scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.F32), dtype=t.uint8, device="cuda")
+            ab.adlbr_step_explicit(h, u, scratch, ab.F32, d, 4)
+        b = ab.adlbr_batch_create(hs, us, dts, autotune=True)
+        _, ms, pts, ntiles = ab.adlbr_batch_config(b)
+        assert pts == sum(int(np.prod(ITEMS[k][0])) for k in keep) and ntiles > 0 and ms > 0
+        ab.adlbr_batch_step(b, 4)
+        t.cuda.synchronize()
+        for k, (u, r) in enumerate(zip(us, ref)):
+            err = (u - r).abs().max().item() / r.abs().max().item()
+            assert err <= 1e-6, (keep[k], err)
+    finally:
+        if b:
+            ab.adlbr_batch_destroy(b)
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
+
+
 def test_batch_matches_oracle():
     t = torch()
     hs, us, dts, seen = _setup()
