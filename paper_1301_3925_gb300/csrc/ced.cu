@@ -16,6 +16,7 @@
 // gradient and outer product in one pass, and the 2x2 eigen-decomposition
 // fused into the epilogue of the last (y) pass.
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 
@@ -238,11 +239,20 @@ __device__ __forceinline__ void blur_group(const float (&v)[NB + 2 * RR], const 
     }
 }
 
-constexpr int RBY = 8;   // rows per thread in the last (y) pass: 512 groups
+// rows per thread in the last (y) pass of the run-time-radius form (512
+// groups); the compile-time form gives every one of its 768 threads one
+// group of 6 or 5 rows (0.2585 against 0.262 ms with 512 groups of 8)
+constexpr int RBY = 8;
 // outputs per thread in the first three passes of the fused kernel: 8 reads
 // 2r + 8 staged values per 8 outputs (0.267 against 0.286 ms with 4 at
 // 4096^2, sigma 1, rho 4; 16 in the P x pass alone: 0.269)
 constexpr int RBF = 8;
+// outputs per thread in the two sigma passes with compile-time radii: 12,
+// so that the x pass has exactly one 12-column group per thread (96 rows x 8
+// groups = 768) and the y pass one round (90 columns x 8 groups); with 8,
+// half the threads took a second group while the rest waited at the
+// barrier (0.262 against 0.270 ms at 4096^2, bit-identical)
+constexpr int RBS_FIXED = 12;
 
 // S_, R_ > 0: radii fixed at compile time (all loops unrolled, windows in
 // registers, constant index arithmetic); 0: taken from g at run time, with
@@ -316,35 +326,36 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         origin(tile + gridDim.x, nx0, ny0);
         load_u_window<S_, R_>(g, nx, ny, nx0, ny0, u, (it & 1) ? sm : sm + g.offU1);
     }
-    // 2. bx = x pass of u (lanes along rows, RBF outputs per thread)
+    constexpr int RBS = fixed ? RBS_FIXED : RBF;
+    // 2. bx = x pass of u (lanes along rows, RBS outputs per thread)
     {
-        const int groups = (g.BW + RBF - 1) / RBF;
+        const int groups = (g.BW + RBS - 1) / RBS;
         for (int i = threadIdx.x; i < g.BH * groups; i += FNT) {
-            const int r = i % g.BH, c0 = (i / g.BH) * RBF;
+            const int r = i % g.BH, c0 = (i / g.BH) * RBS;
             const float *s = U + r * g.UP + c0 + S - SR;
-            float v[RBF + 2 * SR], acc[RBF];
+            float v[RBS + 2 * SR], acc[RBS];
 #pragma unroll
-            for (int j = 0; j < RBF + 2 * SR; ++j) v[j] = (fixed || (j >= SR - S && j < SR + S + RBF)) ? s[j] : 0.f;
-            blur_group<SR, RBF>(v, ts, S, acc);
+            for (int j = 0; j < RBS + 2 * SR; ++j) v[j] = (fixed || (j >= SR - S && j < SR + S + RBS)) ? s[j] : 0.f;
+            blur_group<SR, RBS>(v, ts, S, acc);
 #pragma unroll
-            for (int o = 0; o < RBF; ++o)
+            for (int o = 0; o < RBS; ++o)
                 if (c0 + o < g.BW) B[r * g.BP + c0 + o] = acc[o];
         }
     }
     __syncthreads();
-    // 3. u_sigma = y pass of bx (lanes along columns, RBF rows per thread)
+    // 3. u_sigma = y pass of bx (lanes along columns, RBS rows per thread)
     {
-        const int groups = (g.SH + RBF - 1) / RBF;
+        const int groups = (g.SH + RBS - 1) / RBS;
         for (int i = threadIdx.x; i < g.SW * groups; i += FNT) {
-            const int c = i % g.SW, r0 = (i / g.SW) * RBF;
+            const int c = i % g.SW, r0 = (i / g.SW) * RBS;
             const float *s = B + (r0 + S - SR) * g.BP + c;
-            float v[RBF + 2 * SR], acc[RBF];
+            float v[RBS + 2 * SR], acc[RBS];
 #pragma unroll
-            for (int j = 0; j < RBF + 2 * SR; ++j)
-                v[j] = (fixed || (j >= SR - S && j < SR + S + RBF)) ? s[j * g.BP] : 0.f;
-            blur_group<SR, RBF>(v, ts, S, acc);
+            for (int j = 0; j < RBS + 2 * SR; ++j)
+                v[j] = (fixed || (j >= SR - S && j < SR + S + RBS)) ? s[j * g.BP] : 0.f;
+            blur_group<SR, RBS>(v, ts, S, acc);
 #pragma unroll
-            for (int o = 0; o < RBF; ++o)
+            for (int o = 0; o < RBS; ++o)
                 if (r0 + o < g.SH) US[(r0 + o) * g.SP + c] = acc[o];
         }
     }
@@ -381,23 +392,22 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         }
     }
     __syncthreads();
-    // 6. y pass of Px and D(J) (lanes along columns, RBY rows per thread)
+    // 6. y pass of Px and D(J) (lanes along columns, NB rows per thread)
     {
-        constexpr int groups = FT / RBY;
-        for (int i = threadIdx.x; i < FT * groups; i += FNT) {
-            const int c = i % FT, r0 = (i / FT) * RBY;
-            float J[3][RBY];
+        auto y_group = [&](auto nb, int c, int r0) {
+            constexpr int NB = decltype(nb)::value;
+            float J[3][NB];
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float *s = PX + (ch * g.PH + r0 + R - RR) * g.XP + c;
-                float v[RBY + 2 * RR];
+                float v[NB + 2 * RR];
 #pragma unroll
-                for (int j = 0; j < RBY + 2 * RR; ++j)
-                    v[j] = (fixed || (j >= RR - R && j < RR + R + RBY)) ? s[j * g.XP] : 0.f;
-                blur_group<RR, RBY>(v, tr, R, J[ch]);
+                for (int j = 0; j < NB + 2 * RR; ++j)
+                    v[j] = (fixed || (j >= RR - R && j < RR + R + NB)) ? s[j * g.XP] : 0.f;
+                blur_group<RR, NB>(v, tr, R, J[ch]);
             }
 #pragma unroll
-            for (int o = 0; o < RBY; ++o) {
+            for (int o = 0; o < NB; ++o) {
                 const int64_t z = (int64_t)(y0 + r0 + o) * nx + x0 + c;
                 float dxx, dxy, dyy;
                 d_from_j(J[0][o], J[1][o], J[2][o], alpha, Cc, dxx, dxy, dyy);
@@ -405,6 +415,19 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
                 D[N + z] = dxy;
                 D[2 * N + z] = dyy;
             }
+        };
+        if constexpr (fixed && FNT == 768 && FT == 64) {
+            // every thread takes one group: warps 0-7 six rows each (rows
+            // 0..23), warps 8-23 five rows each (rows 24..63)
+            if (threadIdx.x < 256)
+                y_group(std::integral_constant<int, 6>(), threadIdx.x % FT, (threadIdx.x / FT) * 6);
+            else
+                y_group(std::integral_constant<int, 5>(), (threadIdx.x - 256) % FT,
+                        24 + ((threadIdx.x - 256) / FT) * 5);
+        } else {
+            constexpr int groups = FT / RBY;
+            for (int i = threadIdx.x; i < FT * groups; i += FNT)
+                y_group(std::integral_constant<int, RBY>(), i % FT, (i / FT) * RBY);
         }
     }
     }

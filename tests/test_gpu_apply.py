@@ -51,6 +51,37 @@ def test_apply_fp64(bc, dim):
     assert np.abs(Au - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
+THIN = [(1, 37), (37, 1), (2, 130), (130, 3), (5, 9), (1, 1, 50), (3, 1, 40), (40, 2, 1), (2, 3, 70)]
+
+
+@pytest.mark.parametrize("shape", THIN, ids=["x".join(map(str, s)) for s in THIN])
+@pytest.mark.parametrize("bc", [ab.NEUMANN, ab.PERIODIC])
+@pytest.mark.parametrize("u_dtype", ["float64", "float32"])
+def test_apply_thin_grids(shape, bc, u_dtype):
+    """Grids thinner than a tile or its halo in some direction (one point
+    wide, fewer points than an offset is long, x not a multiple of 4, so no
+    TMA window): FP64 to rounding, FP32 to 1e-5 relative, both boundary
+    rules, with anisotropic fields whose offsets leave the grid."""
+    t = torch()
+    dt_ = getattr(t, u_dtype)
+    if len(shape) == 2:
+        D = synth.smooth_field2d(*shape, seed=7, kappa_min=1, kappa_max=40, lattice=4)
+    else:
+        n = max(shape)
+        D = synth.needle_field3d(n, seed=8, kappa=15.0)[:, :shape[0], :shape[1], :shape[2]]
+    w_t = ab.F64 if u_dtype == "float64" else ab.F32
+    h, seen, _ = build(D, shape, dt_, w_t, bc)
+    try:
+        u = synth.u_uniform(shape, 3)
+        Au, useen = _gpu_apply(h, u, dt_)
+    finally:
+        ab.adlbr_stencils_destroy(h)
+    oo, ow = _oracle_stencils(seen, len(shape))
+    ref = oracle.apply(shape, bc, oo, ow, useen)
+    tol = 1e-13 if u_dtype == "float64" else 1e-5
+    assert np.abs(Au - ref).max() <= tol * max(np.abs(ref).max(), 1e-300)
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_apply_fp32_within_1e5(dim):
     """FP32 u, FP32 weights, FP32 accumulation: relative L-inf error <= 1e-5."""
