@@ -80,6 +80,10 @@ def parse():
     p.add_argument("--no-spectral", action="store_true", help="skip the periodic spectral study")
     p.add_argument("--no-ann", action="store_true", help="skip the A-NN comparison scheme")
     p.add_argument("--precision-steps", type=int, default=100)
+    p.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=2,
+                   help="workload: 2 (default) is the headline CED step and its full line; 1, 3, 4 and 5 "
+                        "run only that workload's measurement (64^2 FP64 steps, the 256^3 precision "
+                        "study, the 2048^2 implicit step, the serving batch) and print it as one line")
     p.add_argument("--cpu-configs", action="store_true",
                    help="only time the oracle on samples of the other workloads (64^2 FP64 build and steps, "
                         "3D steps, CG iterations, batch items), one thread and every host core")
@@ -962,6 +966,41 @@ def profile_unet():
     return 0
 
 
+CONFIG_WORKLOADS = {
+    1: "64x64 FP64 spiral field (kappa 10): stencil build and 10 explicit steps at the stability limit",
+    3: "256^3 needle field (eigenvalues 1, 1/20^2, 1/20^2): build, operator, 100-step precision study "
+       "(FP32, FP16, BF16 u against FP64)",
+    4: "2048^2 implicit step (I + dt A) u = u_n, dt = 200 x the explicit limit, kappa <= 50: CG, "
+       "Jacobi-PCG, U-Net-preconditioned flexible CG to 1e-6",
+    5: "serving batch: 64 images 256^2-2048^2 and 8 volumes 64^3-192^3, one graph launch per step"}
+
+
+def run_config(args):
+    """One workload other than the headline, on one GPU: its measurement as
+    one JSON line (the entry of the full line that covers it)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    peak, peak_src = measured_peaks()
+    if args.config == 1:
+        res = small_measurement()
+        value, unit, hib = res["runs_per_s"], "runs/s", True
+    elif args.config == 3:
+        res = volume_measurement(peak, args.precision_steps)
+        value, unit, hib = 256 ** 3 / (res["precision"]["f32"]["ms_per_step"] * 1e-3) / 1e9, "Gpts/s", True
+    elif args.config == 4:
+        res = implicit_measurement(peak)
+        value, unit, hib = res["cg"]["ms"], "ms", False
+    else:
+        res = batch_measurement(peak)
+        value, unit, hib = res["gpts"], "Gpts/s", True
+    print(json.dumps({"config_id": args.config, "workload": CONFIG_WORKLOADS[args.config], "value": value,
+                      "unit": unit, "higher_is_better": hib, "n_gpus": 1, "dtype": "see result",
+                      "data": "synthetic", "peak_hbm_gbs": peak, "peak_source": peak_src, "result": res}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -979,6 +1018,8 @@ def main():
         return profile_fcg()
     if args.profile_gather:
         return profile_gather()
+    if args.config != 2:
+        return run_config(args)
 
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
