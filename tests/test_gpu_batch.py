@@ -130,3 +130,56 @@ def test_batch_rejects_bad_input():
     finally:
         for h in hs:
             ab.adlbr_stencils_destroy(h)
+
+
+def test_batch_full_size_serving_workload():
+    """The serving batch at its full size (64 images of sides 256-2048 and 8
+    volumes of sides 64-192, 137 M points, F16 weights, FP32 u), in the launch
+    configuration the bench times (autotuned shapes, graph launches): two
+    batched steps equal the same steps issued item by item to 1e-6 on every
+    item, and the smallest image and the smallest volume equal the oracle's
+    steps on the GPU's own stencils to 1e-5."""
+    t = torch()
+    items = synth.batch_items()
+    hs, us, dts, ref, shapes = [], [], [], [], []
+    b = None
+    try:
+        for it in items:
+            shape = it["shape"]
+            if it["dim"] == 2:
+                D = synth.smooth_field2d_torch(*shape, it["seed"], 1.0, it["kappa"], 16).reshape(3, -1)
+            else:
+                D = t.from_numpy(synth.needle_field3d(shape[0], it["seed"], kappa=it["kappa"],
+                                                      dtype=np.float32).reshape(6, -1)).cuda()
+            h = ab.adlbr_build_stencils(ab.grid(shape), D, ab.F32, ab.F16)
+            hs.append(h)
+            del D
+            dts.append(1.0 / ab.adlbr_stencils_max_diag(h))
+            us.append(t.rand(int(np.prod(shape)), device="cuda",
+                             generator=t.Generator(device="cuda").manual_seed(it["seed"])))
+            ref.append(us[-1].clone())
+            shapes.append(shape)
+        small2 = min((k for k, s in enumerate(shapes) if len(s) == 2), key=lambda k: np.prod(shapes[k]))
+        small3 = min((k for k, s in enumerate(shapes) if len(s) == 3), key=lambda k: np.prod(shapes[k]))
+        u0 = {k: us[k].double().cpu().numpy() for k in (small2, small3)}
+        for h, u, d in zip(hs, ref, dts):
+            scratch = t.empty(ab.adlbr_step_scratch_bytes(h, ab.F32), dtype=t.uint8, device="cuda")
+            ab.adlbr_step_explicit(h, u, scratch, ab.F32, d, 2)
+        b = ab.adlbr_batch_create(hs, us, dts, autotune=True)
+        assert ab.adlbr_batch_config(b)[2] == sum(int(np.prod(s)) for s in shapes)
+        ab.adlbr_batch_step(b, 2)
+        t.cuda.synchronize()
+        for k, (u, r) in enumerate(zip(us, ref)):
+            err = (u - r).abs().max().item() / r.abs().max().item()
+            assert err <= 1e-6, (k, shapes[k], err)
+        for k in (small2, small3):
+            oo, ow = export(hs[k], shapes[k], ab.F16)
+            uo = oracle.step_explicit(shapes[k], ab.NEUMANN, oo, ow, u0[k].reshape(shapes[k]), dts[k], 2)
+            out = us[k].double().cpu().numpy().reshape(shapes[k])
+            err = np.abs(out - uo).max() / np.abs(uo).max()
+            assert err <= 1e-5, (k, shapes[k], err)
+    finally:
+        if b:
+            ab.adlbr_batch_destroy(b)
+        for h in hs:
+            ab.adlbr_stencils_destroy(h)
