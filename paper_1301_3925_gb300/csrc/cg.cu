@@ -103,13 +103,26 @@ __global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *
     }
 }
 
-// alpha = rr / <p, q>
+// alpha = rr / <p, q>.  V4: four consecutive elements per step (16-byte
+// loads; every vector 16-byte aligned and N a multiple of 4).
+template <bool V4>
 __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__ p,
                                             const float *__restrict__ q, double *partials, CgState *S) {
     if (S->conv) return;
     FFAcc s;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT)
-        ff_add_prod(s, p[i], q[i]);
+    const int64_t i0 = (int64_t)blockIdx.x * RT + threadIdx.x, stride = (int64_t)gridDim.x * RT;
+    if constexpr (V4) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
+        for (int64_t i = i0; i < N / 4; i += stride) {
+            const float4 a = p4[i], b = q4[i];
+            ff_add_prod(s, a.x, b.x);
+            ff_add_prod(s, a.y, b.y);
+            ff_add_prod(s, a.z, b.z);
+            ff_add_prod(s, a.w, b.w);
+        }
+    } else {
+        for (int64_t i = i0; i < N; i += stride) ff_add_prod(s, p[i], q[i]);
+    }
     double part = block_sum_ff(s);
     double tot;
     if (finish_reduction(part, partials, &S->count, tot)) {
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__
 }
 
 // x += alpha p ; r -= alpha q ; rr_new = <r, r> (JAC: and <r, z>) ; beta ; flag
-template <bool JAC>
+template <bool JAC, bool V4>
 __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, const float *__restrict__ p,
                                             float *__restrict__ r, const float *__restrict__ q,
                                             const float *__restrict__ inv_d, double *partials,
@@ -127,12 +140,35 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
     if (S->conv) return;
     const float alpha = (float)S->alpha;
     FFAcc s, sz;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        x[i] += alpha * p[i];
-        float ri = r[i] - alpha * q[i];
-        r[i] = ri;
+    const int64_t i0 = (int64_t)blockIdx.x * RT + threadIdx.x, stride = (int64_t)gridDim.x * RT;
+    auto one = [&](float &xi, float pi, float &ri, float qi, float di) {
+        xi += alpha * pi;
+        ri = ri - alpha * qi;
         ff_add_prod(s, ri, ri);
-        if (JAC) ff_add_prod(sz, ri, ri * inv_d[i]);
+        if (JAC) ff_add_prod(sz, ri, ri * di);
+    };
+    if constexpr (V4) {
+        float4 *x4 = reinterpret_cast<float4 *>(x), *r4 = reinterpret_cast<float4 *>(r);
+        const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
+        const float4 *d4 = reinterpret_cast<const float4 *>(inv_d);
+        for (int64_t i = i0; i < N / 4; i += stride) {
+            float4 xv = x4[i], rv = r4[i];
+            const float4 pv = p4[i], qv = q4[i];
+            const float4 dv = JAC ? d4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            one(xv.x, pv.x, rv.x, qv.x, dv.x);
+            one(xv.y, pv.y, rv.y, qv.y, dv.y);
+            one(xv.z, pv.z, rv.z, qv.z, dv.z);
+            one(xv.w, pv.w, rv.w, qv.w, dv.w);
+            x4[i] = xv;
+            r4[i] = rv;
+        }
+    } else {
+        for (int64_t i = i0; i < N; i += stride) {
+            float xi = x[i], ri = r[i];
+            one(xi, p[i], ri, q[i], JAC ? inv_d[i] : 0.f);
+            x[i] = xi;
+            r[i] = ri;
+        }
     }
     double part = block_sum_ff(s);
     double tot, rz = 0.0;
@@ -160,16 +196,34 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
 
 // p <- z + beta p (z = r, or r / d) ; q <- p (QP: for the scatter operator,
 // which accumulates dt A p into q; the gather operator writes q itself)
-template <bool JAC, bool QP>
+template <bool JAC, bool QP, bool V4>
 __global__ void __launch_bounds__(RT) cg_k4(int64_t N, const float *__restrict__ r, const float *__restrict__ inv_d,
                                             float *__restrict__ p, float *__restrict__ q, const CgState *S) {
     if (S->conv) return;
     const float beta = (float)S->beta;
-    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
-        const float zi = JAC ? r[i] * inv_d[i] : r[i];
-        const float pi = zi + beta * p[i];
-        p[i] = pi;
-        if (QP) q[i] = pi;
+    const int64_t i0 = (int64_t)blockIdx.x * RT + threadIdx.x, stride = (int64_t)gridDim.x * RT;
+    if constexpr (V4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(r), *d4 = reinterpret_cast<const float4 *>(inv_d);
+        float4 *p4 = reinterpret_cast<float4 *>(p), *q4 = reinterpret_cast<float4 *>(q);
+        for (int64_t i = i0; i < N / 4; i += stride) {
+            const float4 rv = r4[i], pv = p4[i];
+            float4 z = rv;
+            if (JAC) {
+                const float4 dv = d4[i];
+                z = make_float4(rv.x * dv.x, rv.y * dv.y, rv.z * dv.z, rv.w * dv.w);
+            }
+            const float4 np = make_float4(z.x + beta * pv.x, z.y + beta * pv.y, z.z + beta * pv.z,
+                                          z.w + beta * pv.w);
+            p4[i] = np;
+            if (QP) q4[i] = np;
+        }
+    } else {
+        for (int64_t i = i0; i < N; i += stride) {
+            const float zi = JAC ? r[i] * inv_d[i] : r[i];
+            const float pi = zi + beta * p[i];
+            p[i] = pi;
+            if (QP) q[i] = pi;
+        }
     }
 }
 
@@ -210,6 +264,21 @@ static adlbr_status cg_workspace(adlbr_stencils *s, CgWorkspace &W) {
     a = (a + 255) & ~(uintptr_t)255;
     W.S = (CgState *)a;
     return ADLBR_OK;
+}
+
+// The three vector kernels of one CG iteration after the operator.
+template <bool V4>
+static void cg_vec_iteration(int64_t N, float *x, const CgWorkspace &W, bool jac, bool gather, cudaStream_t cs) {
+    cg_k2<V4><<<vec_blocks(), RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
+    if (jac) {
+        cg_k3<true, V4><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
+        if (gather) cg_k4<true, false, V4><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+        else cg_k4<true, true, V4><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+    } else {
+        cg_k3<false, V4><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
+        if (gather) cg_k4<false, false, V4><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+        else cg_k4<false, true, V4><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
+    }
 }
 
 static const int *conv_flag(const CgState *S) {
@@ -288,6 +357,9 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
         if (restart > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
         prev = relres;
         const int chunk = every > 0 ? every : 8;
+        // 16-byte vector passes when every vector allows them (the workspace
+        // vectors are N floats apart, so N % 4 == 0 aligns them; x is the caller's)
+        const bool v4 = N % 4 == 0 && (uintptr_t)x % 16 == 0;
         auto enqueue_chunk = [&](cudaStream_t cs) -> adlbr_status {
             for (int k = 0; k < chunk; ++k) {
                 if (gather) {
@@ -296,17 +368,10 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
                 } else if (adlbr_status e = launch_accumulate(s, W.p, W.q, ADLBR_F32, dt, conv_flag(W.S), cs)) {
                     return e;
                 }
-                cg_k2<<<vec_blocks(), RT, 0, cs>>>(N, W.p, W.q, W.partials, W.S);
-                if (jac) {
-                    cg_k3<true><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2, W.S);
-                    if (gather) cg_k4<true, false><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                    else cg_k4<true, true><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                } else {
-                    cg_k3<false><<<vec_blocks(), RT, 0, cs>>>(N, x, W.p, W.r, W.q, W.inv_d, W.partials, W.partials2,
-                                                    W.S);
-                    if (gather) cg_k4<false, false><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                    else cg_k4<false, true><<<vec_blocks(), RT, 0, cs>>>(N, W.r, W.inv_d, W.p, W.q, W.S);
-                }
+                if (v4)
+                    cg_vec_iteration<true>(N, x, W, jac, gather, cs);
+                else
+                    cg_vec_iteration<false>(N, x, W, jac, gather, cs);
             }
             ADLBR_CUDA(cudaGetLastError());
             return ADLBR_OK;
