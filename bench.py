@@ -62,7 +62,10 @@ def fp32_peak_tops():
 # second warm-up step of this benchmark's CED step)
 TRAFFIC_4096 = {"ced_fused_kernel": 67.344e6 + 139.785e6, "build2d_kernel": 201.441e6 + 222.316e6,
                 # operator + finalize
-                "explicit_step": 402.739e6 + 48.194e6 + 134.228e6 + 19.020e6}
+                "explicit_step": 402.739e6 + 48.194e6 + 134.228e6 + 19.020e6,
+                # fused build and operator + finalize (the memset's 67 MB write is
+                # not a kernel and is not counted)
+                "build_step": 336.232e6 + 291.659e6 + 134.228e6 + 19.020e6}
 
 
 def parse():
@@ -1044,12 +1047,11 @@ def main():
     S = (CED["sigma"], CED["rho"], CED["alpha"], CED["C"])
 
     def step():
-        # adlbr_ced_stencils (tensor stage + stencil build) as its two calls,
-        # so that each kernel is timed on its own; then the explicit step
+        # the tensor stage, then the stencil build and the explicit step in
+        # one call (one fused kernel for this workload), each timed on its own
         nonlocal h
         ab.adlbr_ced_tensor(g, u, Dbuf, *S, scratch)
-        h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
-        ab.adlbr_step_explicit(h, u, acc, ab.F32, CED["dt"], 1)
+        h = ab.adlbr_build_step_explicit(g, Dbuf, ab.F32, ab.F16, h, u, acc, CED["dt"])
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -1057,7 +1059,7 @@ def main():
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -1076,10 +1078,8 @@ def main():
         e[0].record(stream)
         ab.adlbr_ced_tensor(g, u, Dbuf, *S, scratch)
         e[1].record(stream)
-        h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
+        h = ab.adlbr_build_step_explicit(g, Dbuf, ab.F32, ab.F16, h, u, acc, CED["dt"])
         e[2].record(stream)
-        ab.adlbr_step_explicit(h, u, acc, ab.F32, CED["dt"], 1)
-        e[3].record(stream)
     end.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -1089,9 +1089,25 @@ def main():
     total_ms = start.elapsed_time(end)
     total_ms = allmax(ws, total_ms)
     st_tensor = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    st_build = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    st_step = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+    st_bstep = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     ms_step = total_ms / K
+
+    # the same step as three calls (tensor, build, explicit step with the
+    # stand-alone operator), each timed: the stages before the fusion
+    ev2 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(10)]
+    u_side = u.clone()
+    for e in ev2:
+        e[0].record(stream)
+        ab.adlbr_ced_tensor(g, u_side, Dbuf, *S, scratch)
+        e[1].record(stream)
+        h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
+        e[2].record(stream)
+        ab.adlbr_step_explicit(h, u_side, acc, ab.F32, CED["dt"], 1)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    del u_side
+    st_build = float(np.mean([e[1].elapsed_time(e[2]) for e in ev2[2:]]))
+    st_step = float(np.mean([e[2].elapsed_time(e[3]) for e in ev2[2:]]))
     value = job_value(ws, N, ms_step)
 
     # roofline of the dominant kernel; the others beside it
@@ -1106,16 +1122,25 @@ def main():
             return {"kernel": name, "bound": "alu", "achieved": a, "peak": pk, "unit": "Tops/s",
                     "frac": a / pk, "traffic": TRAFFIC_4096.get(name), "peak_source": pk_src,
                     "ops_per_point": ALU_OPS_PER_POINT, "units_per_launch": N}
-        bpp = {"build2d_kernel": 12 + 8 + 8, "explicit_step": 4 + 16 + 4}[name]
+        # build_step: D in 12 + stencils out 16 + u in 4 + u out 4
+        bpp = {"build_step": 12 + 16 + 4 + 4, "build2d_kernel": 12 + 8 + 8, "explicit_step": 4 + 16 + 4}[name]
         a = bpp * N / (ms * 1e-3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
                 "traffic": TRAFFIC_4096.get(name), "peak_source": peak_src, "bytes_per_point": bpp,
                 "units_per_launch": N}
 
-    stage_ms = {"ced_fused_kernel": st_tensor, "build2d_kernel": st_build, "explicit_step": st_step}
+    stage_ms = {"ced_fused_kernel": st_tensor, "build_step": st_bstep}
     dom = max(stage_ms, key=stage_ms.get)
     roof = roof_of(dom, stage_ms[dom])
     roof["others"] = [roof_of(k, v) for k, v in stage_ms.items() if k != dom]
+    if dom == "build_step" or "build_step" in stage_ms:
+        for r in [roof] + roof["others"]:
+            if r["kernel"] == "build_step":
+                r["kernels"] = "memset + build_accumulate2d_tma (stencil build fused into the operator) + finalize"
+    unfused = {"build2d_kernel": roof_of("build2d_kernel", st_build), "explicit_step": roof_of("explicit_step", st_step),
+               "build_ms": st_build, "explicit_step_ms": st_step,
+               "note": "the same step as separate calls (build, then the stand-alone operator), 8 steps "
+                       "after 2 untimed, for comparison"}
     step_gbs = 24 * N / (st_step * 1e-3) / 1e9
 
     # the operator alone on the step's stencils (adlbr_apply: zero Au, accumulate)
@@ -1156,8 +1181,7 @@ def main():
         def step_on(buf):
             nonlocal h
             ab.adlbr_ced_tensor(g, buf, Dbuf, *S, scratch)
-            h = ab.adlbr_build_stencils(g, Dbuf, ab.F32, ab.F16, out=h)
-            ab.adlbr_step_explicit(h, buf, acc, ab.F32, CED["dt"], 1)
+            h = ab.adlbr_build_step_explicit(g, Dbuf, ab.F32, ab.F16, h, buf, acc, CED["dt"])
 
         def run(n):
             done_out = [None] * 3
@@ -1213,20 +1237,23 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value,
                 "value_is": "one CED step of the hot path (tensor stage, stencil build, explicit step with "
-                            "the operator) on the 4096^2 image, points per second; the operator alone is "
-                            "apply_gpts / apply_frac_hbm",
+                            "the operator; the build runs inside the operator's kernel) on the 4096^2 image, "
+                            "points per second; the operator alone is apply_gpts / apply_frac_hbm",
                 "apply_gpts": apply_sub["gpts"], "apply_frac_hbm": apply_sub["frac_hbm"],
                 "unit": UNIT, "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
-                # per step: the fused tensor kernel, the stencil build, the operator
-                # and the finalize kernel
-                "gpu_launches": K * 4,
-                "stages_ms": {"tensor": st_tensor, "build": st_build, "explicit_step": st_step},
+                # per step: the fused tensor kernel, the stencil build fused into
+                # the operator, and the finalize kernel
+                "gpu_launches": K * 3,
+                "stages_ms": {"tensor": st_tensor, "build_step": st_bstep},
+                "unfused": unfused,
                 "explicit_step": {"gpts": N / (st_step * 1e-3) / 1e9, "gbs": step_gbs,
-                                  "frac_hbm": step_gbs / peak, "bytes_per_point": 24},
+                                  "frac_hbm": step_gbs / peak, "bytes_per_point": 24,
+                                  "note": "the stand-alone explicit step (memset, operator, finalize) "
+                                          "on the step's stencils"},
                 "apply": apply_sub, "implicit": implicit, "volume3d": volume, "batch": batch,
                 "ced3d": ced3d, "spectral": spectral_study, "ann": ann_study, "small_64_fp64": small}
         print(json.dumps(line))

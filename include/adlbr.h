@@ -253,6 +253,29 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
                                  double dt, int nsteps, cudaStream_t stream);
 
 /*
+ * adlbr_build_step_explicit -- the stencils of D built into *s (Sec. 2, as
+ * adlbr_build_stencils) and one explicit step u <- u - dt A u with them
+ * (Sec. 4.4, as adlbr_step_explicit), the step of a loop that re-stencils
+ * every step (the CED loop of Sec. 4.4).
+ *
+ *  g, D, D_t, w_t, s  as adlbr_build_stencils (*s == NULL allocates).
+ *  u        device FP32, N elements, updated in place.
+ *  scratch  device, adlbr_step_scratch_bytes(*s, ADLBR_F32) bytes (N floats).
+ * For a 2D grid with FP32 D, F16 weights, a non-periodic boundary, nx % 4 ==
+ * 0 and u 16-byte aligned (and the handle not set to the gather form) the
+ * construction runs inside the operator's kernel: each point's stencil is
+ * built, stored in the handle and applied by the same thread.  Otherwise
+ * this is adlbr_build_stencils followed by adlbr_step_explicit.  Either way
+ * the stored stencils are bit for bit those of adlbr_build_stencils, and u
+ * equals the two-call result to FP32 rounding (the order of the atomic
+ * additions).  Errors as the two calls; a failed build is reported, as
+ * there, by adlbr_stencils_check.
+ */
+adlbr_status adlbr_build_step_explicit(const adlbr_grid *g, const void *D, adlbr_dtype D_t, adlbr_dtype w_t,
+                                       adlbr_stencils **s, float *u, void *scratch, double dt,
+                                       cudaStream_t stream);
+
+/*
  * adlbr_step_explicit_noalloc -- adlbr_step_explicit without any allocation.
  *
  * The paper has no counterpart: this entry point is for callers that cannot

@@ -69,6 +69,8 @@ def lib():
             "adlbr_stencils_export": (_i32, [_vp, _vp, _vp, _vp]),
             "adlbr_stencils_destroy": (_i32, [_vp]),
             "adlbr_apply": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+            "adlbr_build_step_explicit": (_i32, [ctypes.POINTER(Grid), _vp, _i32, _i32, ctypes.POINTER(_vp), _vp,
+                                                 _vp, ctypes.c_double, _vp]),
             "adlbr_stencils_set_operator": (_i32, [_vp, _i32]),
             "adlbr_stencils_get_operator": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
             "adlbr_step_scratch_bytes": (ctypes.c_size_t, [_vp, _i32]),
@@ -307,6 +309,15 @@ def adlbr_ced_step(h, g, u, scratch, sigma, rho, alpha, C, dt, nsteps, w_t, stre
     _check(lib().adlbr_ced_step(ctypes.byref(hh), ctypes.byref(g), _ptr(u), _ptr(scratch),
                                 float(sigma), float(rho), float(alpha), float(C), float(dt),
                                 int(nsteps), w_t, _stream(stream)))
+    return hh.value
+
+
+def adlbr_build_step_explicit(g, D, D_t, w_t, h, u, scratch, dt, stream=None):
+    """Stencils of D into h (None allocates) and one explicit step of the FP32
+    vector u; returns the handle."""
+    hh = _vp(h)
+    _check(lib().adlbr_build_step_explicit(ctypes.byref(g), _ptr(D), D_t, w_t, ctypes.byref(hh), _ptr(u),
+                                           _ptr(scratch), float(dt), _stream(stream)))
     return hh.value
 
 

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256) build_ann2d_kernel(int64_t N, const T *__
 
 adlbr_status launch_build_ann2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st) {
     ADLBR_NVTX("build");
+    stencils_changed(s);
     if (s->dim != 2 || !s->offs3) return fail(ADLBR_E_INTERNAL, "A-NN build on a handle without a third-offset plane");
     const int threads = 256;
     const unsigned blocks = blocks_for(s->N, threads);

@@ -55,6 +55,11 @@ static int64_t npoints(const adlbr_grid *g) {
     return g->n[0] * g->n[1] * (g->dim == 3 ? g->n[2] : 1);
 }
 
+void stencils_changed(adlbr_stencils *s) {
+    if (s->pull) s->pull->built = false;
+    s->applies_since_build = 0;
+}
+
 // *ps == NULL: allocates a handle for grid g, weight type w_t and scheme.
 // *ps != NULL: checks that it matches (and takes g's boundary rule).
 static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_stencils **ps,
@@ -66,9 +71,6 @@ static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_s
         if (!same) return fail(ADLBR_E_SHAPE, "handle does not match the grid / weight type / scheme");
         if (s->bc != g->bc) pull_free(s);
         s->bc = g->bc;
-        // the stencils are about to change: the gather table no longer matches
-        if (s->pull) s->pull->built = false;
-        s->applies_since_build = 0;
         return ADLBR_OK;
     }
     s = new (std::nothrow) adlbr_stencils();
@@ -101,6 +103,19 @@ static adlbr_status acquire_handle(const adlbr_grid *g, adlbr_dtype w_t, adlbr_s
 }  // namespace adlbr
 
 using namespace adlbr;
+
+// Stencils of D into s, then one explicit step of u (FP32) with acc as the
+// accumulator: one fused kernel where the handle allows it.
+static adlbr_status build_then_step(adlbr_stencils *s, const void *D, adlbr_dtype D_t, float *u, float *acc,
+                                    double dt, cudaStream_t stream) {
+    bool fused = false;
+    if (D_t == ADLBR_F32)
+        if (adlbr_status st = launch_build_accumulate2d(s, (const float *)D, u, acc, dt, &fused, stream)) return st;
+    if (fused) return launch_finalize(s, u, acc, ADLBR_F32, stream);
+    adlbr_status st = s->dim == 2 ? launch_build2d(s, D, D_t, stream) : launch_build3d(s, D, D_t, stream);
+    if (st != ADLBR_OK) return st;
+    return adlbr_step_explicit(s, u, acc, ADLBR_F32, dt, 1, stream);
+}
 
 extern "C" {
 
@@ -228,6 +243,28 @@ adlbr_status adlbr_stencils_get_operator(const adlbr_stencils *s, int *form, int
     if (adlbr_status st = check_handle(s)) return st;
     if (form) *form = s->op_form;
     if (gather_ready) *gather_ready = pull_ready(s) ? 1 : 0;
+    return ADLBR_OK;
+}
+
+adlbr_status adlbr_build_step_explicit(const adlbr_grid *g, const void *D, adlbr_dtype D_t, adlbr_dtype w_t,
+                                       adlbr_stencils **out, float *u, void *scratch, double dt,
+                                       cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_build_step_explicit");
+    if (!out || !D || !u || !scratch) return fail(ADLBR_E_ARG, "null argument");
+    if (!valid_grid(g)) return fail(ADLBR_E_SHAPE, "invalid grid");
+    if (D_t != ADLBR_F32 && D_t != ADLBR_F64) return fail(ADLBR_E_ARG, "D must be F32 or F64");
+    if (w_t != ADLBR_F32 && w_t != ADLBR_F64 && w_t != ADLBR_F16)
+        return fail(ADLBR_E_ARG, "weights must be F64, F32 or F16");
+    if (!(dt >= 0.0)) return fail(ADLBR_E_ARG, "bad dt");
+    const bool fresh = *out == nullptr;
+    adlbr_stencils *s = *out;
+    if (adlbr_status e = acquire_handle(g, w_t, &s)) return e;
+    adlbr_status st = build_then_step(s, D, D_t, u, (float *)scratch, dt, stream);
+    if (st != ADLBR_OK) {
+        if (fresh) adlbr_stencils_destroy(s);
+        return st;
+    }
+    *out = s;
     return ADLBR_OK;
 }
 
@@ -383,9 +420,15 @@ adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, v
     const bool fresh = *s == nullptr;
     if (adlbr_status st = acquire_handle(g, w_t, s)) return st;
     for (int k = 0; k < nsteps; ++k) {
-        // tensor stage, stencil construction, one explicit step
-        adlbr_status st = launch_ced_build(*s, u, sigma, rho, alpha, C, scratch, D, stream);
-        if (st == ADLBR_OK) st = adlbr_step_explicit(*s, u, acc, ADLBR_F32, dt, 1, stream);
+        // tensor stage, stencil construction, one explicit step; in 2D the
+        // construction and the operator run as one kernel where the handle
+        // allows it (F16 weights, a TMA window)
+        adlbr_status st =
+            g->dim == 2
+                ? launch_ced_tensor((int)g->n[0], (int)g->n[1], u, D, sigma, rho, alpha, C, scratch, stream)
+                : launch_ced_tensor3d((int)g->n[0], (int)g->n[1], (int)g->n[2], u, D, sigma, rho, alpha, C,
+                                      scratch, stream);
+        if (st == ADLBR_OK) st = build_then_step(*s, D, ADLBR_F32, u, acc, dt, stream);
         if (st != ADLBR_OK) {
             if (fresh) {
                 adlbr_stencils_destroy(*s);

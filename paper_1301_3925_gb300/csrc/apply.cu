@@ -38,6 +38,23 @@ __global__ void __launch_bounds__(NT) apply2d_tiled_tma(int nx, int ny, int bc, 
                                                   blockIdx.y * TH, smem, &map, err);
 }
 
+// The fused build and step: every point's stencil is built from its FP32
+// tensor inside the operator's pass loop (and stored in the handle, F16
+// weights), then used at once; the u window arrives by TMA as above.  One
+// kernel in place of the build and the operator, so the build's arithmetic
+// and the operator's shared-memory traffic share the SMs.
+template <int TW, int TH, int NT, int WX>
+__global__ void __launch_bounds__(NT) build_accumulate2d_tma(int nx, int ny, int bc, float scale,
+                                                             const float *__restrict__ D, int64_t N,
+                                                             short4 *__restrict__ offs, void *__restrict__ wbase,
+                                                             const float *__restrict__ u, float *__restrict__ acc,
+                                                             const __grid_constant__ CUtensorMap map, int *err) {
+    extern __shared__ __align__(128) float smem[];
+    op::tile2d<float, TW, TH, NT, WX, true, true, op::BuildStencil>(
+        nx, ny, bc, scale, offs, nullptr, wbase, ADLBR_F16, u, acc, blockIdx.x * TW, blockIdx.y * TH, smem, &map, err,
+        op::BuildStencil{D, N, offs, wbase});
+}
+
 template <typename UT, int TW, int TH, int NT, int WX, bool F16W>
 __global__ void __launch_bounds__(NT) apply2d_tiled(int nx, int ny, int bc, float scale,
                                                     const short4 *__restrict__ offs,
@@ -358,6 +375,28 @@ adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc
         return accumulate_t<__nv_bfloat16>(s, (const __nv_bfloat16 *)u, (float *)acc, scale, skip, st);
     }
     return fail(ADLBR_E_ARG, "bad u dtype %d", (int)u_t);
+}
+
+adlbr_status launch_build_accumulate2d(adlbr_stencils *s, const float *D, const float *u, float *acc,
+                                       double scale, bool *done, cudaStream_t st) {
+    *done = false;
+    if (s->dim != 2 || s->scheme != ADLBR_SCHEME_ADLBR || s->w_t != ADLBR_F16 || s->bc == ADLBR_PERIODIC ||
+        s->op_form == ADLBR_OP_GATHER)
+        return ADLBR_OK;
+    constexpr int TW = 64, TH = 32, NT = 256, WX = 16;
+    using T = Tile<TW, TH, NT, WX>;
+    CUtensorMap map;
+    if (!tma::encode_2d_f32(&map, u, (int)s->n[0], (int)s->n[1], T::WW, T::WH)) return ADLBR_OK;
+    ADLBR_NVTX("build");
+    stencils_changed(s);
+    ADLBR_CUDA(cudaMemsetAsync(acc, 0, (size_t)s->N * sizeof(float), st));
+    dim3 grid(blocks_for(s->n[0], TW), blocks_for(s->n[1], TH));
+    constexpr size_t smem = 2 * T::P * T::WH * sizeof(float);
+    build_accumulate2d_tma<TW, TH, NT, WX><<<grid, NT, smem, st>>>((int)s->n[0], (int)s->n[1], s->bc, (float)scale, D,
+                                                                   s->N, (short4 *)s->offs, s->w, u, acc, map, s->err);
+    ADLBR_CUDA(cudaGetLastError());
+    *done = true;
+    return ADLBR_OK;
 }
 
 adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, double *acc, double scale,

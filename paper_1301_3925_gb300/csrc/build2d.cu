@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(256) build2d_kernel(int64_t N, const T *__rest
 
 adlbr_status launch_build2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st) {
     ADLBR_NVTX("build");
+    stencils_changed(s);
     const int threads = 256;
     unsigned blocks = blocks_for(s->N, threads);
     if (D_t == ADLBR_F32)

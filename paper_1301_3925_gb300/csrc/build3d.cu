@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(128) build3d_kernel(int64_t N, const T *__rest
 
 adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st) {
     ADLBR_NVTX("build");
+    stencils_changed(s);
     const int threads = 128;
     unsigned blocks = blocks_for(s->N, threads);
     if (D_t == ADLBR_F32)

@@ -280,6 +280,9 @@ inline unsigned blocks_for(int64_t n, int threads) {
 adlbr_status check_handle(const adlbr_stencils *s);
 
 // kernels' host launchers
+// Every build launcher first marks the handle's stencils as changed: the
+// gather table (if any) no longer matches them.
+void stencils_changed(adlbr_stencils *s);
 adlbr_status launch_build2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st);
 adlbr_status launch_build3d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, cudaStream_t st);
 // the A-NN comparison scheme (Sec. 4.1, Remark rem:WG), 2D (ann.cu)
@@ -364,6 +367,12 @@ adlbr_status launch_jacobi_inverse(const adlbr_stencils *s, double dt, float *in
 // a kernel launched with skip != NULL returns at once when *skip != 0.
 adlbr_status launch_accumulate(const adlbr_stencils *s, const void *u, void *acc, adlbr_dtype u_t,
                                double scale, const int *skip, cudaStream_t st);
+// acc = scale A u with the stencils of the FP32 tensor D built (and stored
+// in s) by the same kernel: 2D AD-LBR handles with F16 weights, FP32 u on a
+// non-periodic grid that takes a TMA window, not set to the gather form.
+// *done = false (nothing enqueued) for any other case.
+adlbr_status launch_build_accumulate2d(adlbr_stencils *s, const float *D, const float *u, float *acc,
+                                       double scale, bool *done, cudaStream_t st);
 // acc (double) += scale * A u for FP32 u: the FP64-accumulated operator used to
 // measure true residuals.
 adlbr_status launch_accumulate_f64(const adlbr_stencils *s, const float *u, double *acc, double scale,

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "stencil2d.cuh"
 #include "tma.cuh"
 
 namespace adlbr {
@@ -68,15 +69,28 @@ struct Tile {
 // by moving its bits to the FP32 position and multiplying by 2^112 (exact,
 // subnormal halves included); the per-point power of two and `scale` are
 // applied by one more product, as in load_weights.
-__device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z, float scale,
-                                                   float (&w)[3]) {
-    const uint2 r = reinterpret_cast<const uint2 *>(wbase)[z];
+__device__ __forceinline__ void weights_f16_rec(uint2 r, float scale, float (&w)[3]) {
     const int s = (int)(int8_t)(r.y >> 24);
     const float c = __int_as_float((127 + s) << 23) * scale;
     w[0] = __uint_as_float((r.x & 0xffffu) << 13) * 0x1p112f * c;
     w[1] = __uint_as_float((r.x >> 16) << 13) * 0x1p112f * c;
     w[2] = __uint_as_float((r.y & 0xffffu) << 13) * 0x1p112f * c;
 }
+__device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z, float scale,
+                                                   float (&w)[3]) {
+    weights_f16_rec(reinterpret_cast<const uint2 *>(wbase)[z], scale, w);
+}
+
+// Where tile2d takes each point's stencil from: the handle's arrays (the
+// operator), or the point's tensor, built on the spot and stored (the fused
+// build and step; FP32 tensors, F16 weights).
+struct LoadStencil {};
+struct BuildStencil {
+    const float *D;    // planes Dxx, Dxy, Dyy of N points
+    int64_t N;
+    short4 *offs;      // the handle's stencil storage
+    void *w;
+};
 
 // acc += scale A u over the tile at (x0, y0); every thread of the block
 // calls it (block-wide barriers inside).  offs3: the third offsets of a
@@ -87,14 +101,16 @@ __device__ __forceinline__ void weights_f16_scaled(const void *wbase, int64_t z,
 // One thread waits for the copy (bounded) while the others sleep in the block
 // barrier.  If the wait gives up, the block records ERRBIT_TIMEOUT in *err,
 // waits up to four more bounds for the copy to land, and returns.
-template <typename UT, int TW, int TH, int NT, int WX, bool F16W, bool TMA = false>
+template <typename UT, int TW, int TH, int NT, int WX, bool F16W, bool TMA = false, typename Src = LoadStencil>
 __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, const short4 *__restrict__ offs,
                                        const short2 *__restrict__ offs3, const void *__restrict__ wbase,
                                        adlbr_dtype wt,
                                        const UT *__restrict__ u, float *__restrict__ acc, int x0, int y0,
-                                       float *smem, const CUtensorMap *map = nullptr, int *err = nullptr) {
+                                       float *smem, const CUtensorMap *map = nullptr, int *err = nullptr,
+                                       const Src &src = Src()) {
     using T = Tile<TW, TH, NT, WX>;
     constexpr int WW = T::WW, WH = T::WH, P = T::P;
+    constexpr bool BUILD = std::is_same<Src, BuildStencil>::value;
     float *uw = smem, *aw = smem + WH * P;
     __syncthreads();   // the window of a previous tile may still be read
     const bool periodic = bc == ADLBR_PERIODIC;
@@ -167,11 +183,20 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
         const int ly = ty + k * T::WR * T::WARPS_Y, y = y0 + ly;
         if (!full && (x >= nx || y >= ny)) continue;
         const int64_t z = (int64_t)y * nx + x;
-        const short4 o = offs[z];
+        short4 o;
         float w[3];
-        if (F16W) {
+        if constexpr (BUILD) {
+            // (loading the next pass's tensor one pass ahead measured no faster)
+            static_assert(F16W, "the fused build stores F16 weights");
+            const Built2 bt = build_point2d<float>(src.D[z], src.D[src.N + z], src.D[2 * src.N + z], z, src.offs,
+                                                   src.w, ADLBR_F16, err);
+            o = bt.o;
+            weights_f16_rec(bt.rec, scale, w);
+        } else if (F16W) {
+            o = offs[z];
             weights_f16_scaled(wbase, z, scale, w);
         } else {
+            o = offs[z];
             load_weights<float, 3>(wbase, wt, z, w);
 #pragma unroll
             for (int i = 0; i < 3; ++i) w[i] *= scale;

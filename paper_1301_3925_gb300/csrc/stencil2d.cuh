@@ -101,10 +101,17 @@ constexpr int kMaxCoord = 2047;
 
 }  // namespace s2d
 
+// What build_point2d stored for a point: its offsets and, for F16 weights,
+// its weight record (zeros for the other weight formats).
+struct Built2 {
+    short4 o;
+    uint2 rec;
+};
+
 // Builds and stores the stencil of point i from D = [[a, b], [b, c]].
 template <typename T>
-__device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
-                                              void *wbase, adlbr_dtype wt, int *err) {
+__device__ __forceinline__ Built2 build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
+                                                void *wbase, adlbr_dtype wt, int *err) {
     using namespace s2d;
     using WV = typename WVal<T>::type;
     WV wz[3] = {};
@@ -116,9 +123,9 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
     }
     if (code) {
         offs[i] = make_short4(0, 0, 0, 0);
-        store_weights<3>(wbase, wt, i, wz, 7u);
+        const uint4 r = store_weights<3>(wbase, wt, i, wz, 7u);
         atomicOr(err, code);
-        return;
+        return Built2{make_short4(0, 0, 0, 0), make_uint2(r.x, r.y)};
     }
 
     // (i) approximate Lagrange reduction in FP32 on S / max(a, c): the basis
@@ -182,9 +189,9 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
     for (int k = 0; k < 3; ++k) range |= fabsf(v[k].x) > (float)kMaxCoord || fabsf(v[k].y) > (float)kMaxCoord;
     if (!ok || range) {
         offs[i] = make_short4(0, 0, 0, 0);
-        store_weights<3>(wbase, wt, i, wz, 7u);
+        const uint4 r = store_weights<3>(wbase, wt, i, wz, 7u);
         atomicOr(err, range ? ERRBIT_RANGE : ERRBIT_NOT_CONVERGED);
-        return;
+        return Built2{make_short4(0, 0, 0, 0), make_uint2(r.x, r.y)};
     }
 
     // weights gamma(+-e_k) = -<e_{k+1}, S e_{k+2}> / 2
@@ -214,8 +221,10 @@ __device__ __forceinline__ void build_point2d(T a, T b, T c, int64_t i, short4 *
                 atomicOr(err, ERRBIT_BOUNDS);
         }
     }
-    offs[i] = make_short4((short)(int)v[0].x, (short)(int)v[0].y, (short)(int)v[1].x, (short)(int)v[1].y);
-    store_weights<3>(wbase, wt, i, wz, zmask);
+    const short4 o = make_short4((short)(int)v[0].x, (short)(int)v[0].y, (short)(int)v[1].x, (short)(int)v[1].y);
+    offs[i] = o;
+    const uint4 r = store_weights<3>(wbase, wt, i, wz, zmask);
+    return Built2{o, make_uint2(r.x, r.y)};
 }
 
 }  // namespace adlbr

@@ -15,10 +15,12 @@ __device__ __forceinline__ double neg_half(double v) { return -0.5 * v; }
 __device__ __forceinline__ FF wmax0(FF v) { return (v.hi > 0.f || (v.hi == 0.f && v.lo > 0.f)) ? v : FF{0.f, 0.f}; }
 __device__ __forceinline__ double wmax0(double v) { return fmax(v, 0.0); }
 
-// w[0..K) are the weights (>= 0, +0 where zmask has the bit set).
+// w[0..K) are the weights (>= 0, +0 where zmask has the bit set).  Returns
+// the stored record for the F16 format (its first 8 bytes for K = 3, all 16
+// for K = 6), zeros for the other formats.
 template <int K, typename V>
-__device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64_t i,
-                                              const V (&w)[K], unsigned zmask) {
+__device__ __forceinline__ uint4 store_weights(void *wbase, adlbr_dtype wt, int64_t i,
+                                               const V (&w)[K], unsigned zmask) {
     constexpr int L = (K == 3) ? 4 : 8;
     if (wt == ADLBR_F16) {
         float wf[K];
@@ -49,10 +51,14 @@ __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64
         }
         uint16_t meta = (uint16_t)((zmask & 0xffu) | ((unsigned)(uint8_t)(int8_t)s << 8));
         *reinterpret_cast<uint16_t *>(&h[K]) = meta;
-        if (L == 4)
-            reinterpret_cast<uint2 *>(wbase)[i] = *reinterpret_cast<uint2 *>(h);
-        else
-            reinterpret_cast<uint4 *>(wbase)[i] = *reinterpret_cast<uint4 *>(h);
+        if (L == 4) {
+            const uint2 r = *reinterpret_cast<uint2 *>(h);
+            reinterpret_cast<uint2 *>(wbase)[i] = r;
+            return make_uint4(r.x, r.y, 0u, 0u);
+        }
+        const uint4 r = *reinterpret_cast<uint4 *>(h);
+        reinterpret_cast<uint4 *>(wbase)[i] = r;
+        return r;
     } else if (wt == ADLBR_F32) {
         float v[L];
 #pragma unroll
@@ -74,6 +80,7 @@ __device__ __forceinline__ void store_weights(void *wbase, adlbr_dtype wt, int64
 #pragma unroll
         for (int k = 0; k < L; k += 2) *reinterpret_cast<double2 *>(p + k) = *reinterpret_cast<double2 *>(v + k);
     }
+    return make_uint4(0u, 0u, 0u, 0u);
 }
 
 }  // namespace adlbr

@@ -198,3 +198,88 @@ def test_ced_stencils_bitexact_on_gpu_tensor_4096():
     assert np.array_equal(go, oo), np.argwhere(np.any(go != oo, axis=(1, 2)))[:5]
     assert np.all(np.abs(gw - ow) <= weight_tol(ow, ab.F16, np.abs(Ds).max()))
     assert np.array_equal(outs[1][0], go) and np.array_equal(outs[1][1], gw)
+
+
+def _ced_D(shape, seed):
+    img = synth.fingerprint(max(shape), seed)[:shape[0], :shape[1]]
+    return np.stack(ced.ced_tensor(img, 1.0, 4.0, 1e-4, 1e-5)).reshape(3, -1), img
+
+
+BUILD_STEP_CASES = {
+    # (shape, bc, D dtype, weight type): the first takes the fused kernel
+    "fused": ((96, 160), ab.NEUMANN, "float32", ab.F16),
+    "ragged_fused": ((77, 132), ab.NEUMANN, "float32", ab.F16),
+    "periodic": ((96, 160), ab.PERIODIC, "float32", ab.F16),
+    "nx_not_4": ((96, 158), ab.NEUMANN, "float32", ab.F16),
+    "f32_weights": ((96, 160), ab.NEUMANN, "float32", ab.F32),
+    "f64_tensor": ((96, 160), ab.NEUMANN, "float64", ab.F16),
+}
+
+
+@pytest.mark.parametrize("case", list(BUILD_STEP_CASES))
+def test_build_step_equals_build_then_step(case):
+    """adlbr_build_step_explicit against adlbr_build_stencils followed by
+    adlbr_step_explicit on the same CED tensor: stencils bit for bit, u to
+    FP32 rounding, for the fused kernel and for every fallback."""
+    from gpu_helpers import export
+    t = torch()
+    shape, bc, ddt, wt = BUILD_STEP_CASES[case]
+    Dn, img = _ced_D(shape, 13)
+    g = ab.grid(shape, bc)
+    D = dev(Dn, getattr(t, ddt))
+    Dt = ab.F32 if ddt == "float32" else ab.F64
+    dt = 0.02
+    u1 = dev(img.ravel(), t.float32)
+    u2 = u1.clone()
+    h1 = h2 = None
+    try:
+        h1 = ab.adlbr_build_stencils(g, D, Dt, wt)
+        sc1 = t.empty(ab.adlbr_step_scratch_bytes(h1, ab.F32), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(h1, u1, sc1, ab.F32, dt, 1)
+        sc2 = t.empty_like(sc1)
+        h2 = ab.adlbr_build_step_explicit(g, D, Dt, wt, None, u2, sc2, dt)
+        h2 = ab.adlbr_build_step_explicit(g, D, Dt, wt, h2, u2, sc2, dt)   # a second step, in place
+        ab.adlbr_step_explicit(h1, u1, sc1, ab.F32, dt, 1)
+        ab.adlbr_stencils_check(h1)
+        ab.adlbr_stencils_check(h2)
+        o1, w1 = export(h1, shape, wt)
+        o2, w2 = export(h2, shape, wt)
+    finally:
+        for h in (h1, h2):
+            if h:
+                ab.adlbr_stencils_destroy(h)
+    assert np.array_equal(o1, o2)
+    assert np.array_equal(w1, w2)
+    err = (u1 - u2).abs().max().item() / u1.abs().max().item()
+    assert err <= 1e-6, err
+
+
+def test_build_step_reports_a_bad_tensor():
+    """A tensor that is not positive definite at one point: the fused kernel
+    reports it as the build does (ADLBR_E_NOT_SPD from adlbr_stencils_check),
+    gives that point the zero stencil, and steps every other point."""
+    t = torch()
+    shape = (64, 96)
+    Dn, img = _ced_D(shape, 17)
+    Dn = Dn.copy()
+    Dn[0, 700] = -1.0
+    g = ab.grid(shape)
+    D = dev(Dn, t.float32)
+    u1 = dev(img.ravel(), t.float32)
+    u2 = u1.clone()
+    h1 = h2 = None
+    try:
+        h1 = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+        sc1 = t.empty(ab.adlbr_step_scratch_bytes(h1, ab.F32), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(h1, u1, sc1, ab.F32, 0.02, 1)
+        h2 = ab.adlbr_build_step_explicit(g, D, ab.F32, ab.F16, None, u2, t.empty_like(sc1), 0.02)
+        for h in (h1, h2):
+            with pytest.raises(ab.AdlbrError) as ei:
+                ab.adlbr_stencils_check(h)
+            assert ei.value.status == 3
+    finally:
+        for h in (h1, h2):
+            if h:
+                ab.adlbr_stencils_destroy(h)
+    err = (u1 - u2).abs().max().item() / u1.abs().max().item()
+    assert err <= 1e-6, err

@@ -321,3 +321,35 @@ def test_cg_with_gather_operator():
         xg, itg = xs[(ab.OP_GATHER, pc)]
         assert abs(its - itg) <= 3
         assert np.abs(xsc - xg).max() <= 1e-4 * np.abs(xsc).max()
+
+
+def test_gather_table_follows_rebuilds_inside_ced_steps():
+    """adlbr_ced_step rebuilds the stencils at every step of one call: with the
+    gather form asked for, every step must use a table of its own stencils.
+    Four steps in one call equal four calls of one step each (each call
+    builds the table afresh), bit for bit (the gather form is deterministic),
+    and equal the scatter form's four steps to FP32 rounding."""
+    t = torch()
+    shape = (96, 160)
+    g = ab.grid(shape)
+    img = synth.fingerprint(160, 21)[:96, :160].astype(np.float32)
+    P = (1.0, 4.0, 1e-4, 1e-5, 0.02)
+
+    def run(form, calls, per_call):
+        u = t.from_numpy(img.ravel().copy()).cuda()
+        scratch = t.empty(ab.adlbr_ced_scratch_bytes(g), dtype=t.uint8, device="cuda")
+        h = ab.adlbr_ced_stencils(None, g, u, scratch, *P[:4], ab.F16)
+        try:
+            ab.adlbr_stencils_set_operator(h, form)
+            for _ in range(calls):
+                h = ab.adlbr_ced_step(h, g, u, scratch, *P, per_call, ab.F16)
+            t.cuda.synchronize()
+        finally:
+            ab.adlbr_stencils_destroy(h)
+        return u.cpu().numpy()
+
+    one_call = run(ab.OP_GATHER, 1, 4)
+    four_calls = run(ab.OP_GATHER, 4, 1)
+    scatter = run(ab.OP_SCATTER, 1, 4)
+    assert np.array_equal(one_call, four_calls)
+    assert np.abs(one_call - scatter).max() <= 1e-5 * np.abs(scatter).max()
