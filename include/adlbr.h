@@ -269,7 +269,9 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
  * the stored stencils are bit for bit those of adlbr_build_stencils, and u
  * equals the two-call result to FP32 rounding (the order of the atomic
  * additions).  Errors as the two calls; a failed build is reported, as
- * there, by adlbr_stencils_check.
+ * there, by adlbr_stencils_check.  If that check returns ADLBR_E_TIMEOUT (a
+ * tile's window copy never arrived), the tiles concerned were neither built
+ * nor stepped: the stencils and u are then undefined.
  */
 adlbr_status adlbr_build_step_explicit(const adlbr_grid *g, const void *D, adlbr_dtype D_t, adlbr_dtype w_t,
                                        adlbr_stencils **s, float *u, void *scratch, double dt,
