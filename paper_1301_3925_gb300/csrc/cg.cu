@@ -39,13 +39,14 @@ struct CgState {
 };
 
 // (Re)start from the true residual: r = b - (x + dt A x) evaluated in FP64
-// (acc holds dt A x accumulated in FP64), rounded once to FP32; p = r.
+// (acc holds dt A x accumulated in FP64 -- or in FP32 for the first round,
+// AT = float), rounded once to FP32; p = r.
 // rr_new = |r|^2 of the FP64 residual, rr = |r|^2 of its FP32 copy, bb = |b|^2;
 // conv = 1 when the true residual already meets the tolerance.
-template <bool JAC>
+template <bool JAC, typename AT>
 __global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *__restrict__ b,
                                                         const float *__restrict__ x,
-                                                        const double *__restrict__ acc,
+                                                        const AT *__restrict__ acc,
                                                         const float *__restrict__ inv_d,
                                                         float *__restrict__ r, float *__restrict__ p,
                                                         double *partials, double *partials2,
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(RT) cg_restart_kernel(int64_t N, const float *
     double s_true = 0.0, s_rr = 0.0, s_bb = 0.0, s_rz = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < N; i += (int64_t)gridDim.x * RT) {
         const double bi = b[i];
-        const double ri = bi - ((double)x[i] + acc[i]);
+        const double ri = bi - ((double)x[i] + (double)acc[i]);
         const float rf = (float)ri;
         r[i] = rf;
         const float zf = JAC ? rf * inv_d[i] : rf;
@@ -335,19 +336,36 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
     CgState host = {};
     int total_iters = 0;
     double relres = INFINITY, prev = INFINITY;
+    int round_iters = 0;   // CG iterations of the last round
     bool cg_converged = false;
     const int kMaxRestarts = 3;
     for (int restart = 0; restart <= kMaxRestarts; ++restart) {
+        // The first residual only starts CG, so it takes the FP32 operator;
+        // every later round measures the true residual with the operator
+        // accumulated in FP64, and only those decide convergence.
+        const bool first32 = restart == 0;
         init.max_iters = maxit - total_iters;
         ADLBR_CUDA(cudaMemcpyAsync(W.S, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
-        ADLBR_CUDA(cudaMemsetAsync(W.acc64, 0, N * sizeof(double), st));
-        if (adlbr_status e = launch_accumulate_f64(s, x, W.acc64, dt, st)) return e;
-        if (jac)
-            cg_restart_kernel<true><<<vec_blocks(), RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
-                                                       W.partials2, W.partials3, W.partials4, W.S);
-        else
-            cg_restart_kernel<false><<<vec_blocks(), RT, 0, st>>>(N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials,
-                                                        W.partials2, W.partials3, W.partials4, W.S);
+        if (first32) {
+            float *acc32 = W.q;   // q is set from p below
+            ADLBR_CUDA(cudaMemsetAsync(acc32, 0, N * sizeof(float), st));
+            if (adlbr_status e = launch_accumulate(s, x, acc32, ADLBR_F32, dt, nullptr, st)) return e;
+            if (jac)
+                cg_restart_kernel<true, float><<<vec_blocks(), RT, 0, st>>>(
+                    N, b, x, acc32, W.inv_d, W.r, W.p, W.partials, W.partials2, W.partials3, W.partials4, W.S);
+            else
+                cg_restart_kernel<false, float><<<vec_blocks(), RT, 0, st>>>(
+                    N, b, x, acc32, W.inv_d, W.r, W.p, W.partials, W.partials2, W.partials3, W.partials4, W.S);
+        } else {
+            ADLBR_CUDA(cudaMemsetAsync(W.acc64, 0, N * sizeof(double), st));
+            if (adlbr_status e = launch_accumulate_f64(s, x, W.acc64, dt, st)) return e;
+            if (jac)
+                cg_restart_kernel<true, double><<<vec_blocks(), RT, 0, st>>>(
+                    N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials, W.partials2, W.partials3, W.partials4, W.S);
+            else
+                cg_restart_kernel<false, double><<<vec_blocks(), RT, 0, st>>>(
+                    N, b, x, W.acc64, W.inv_d, W.r, W.p, W.partials, W.partials2, W.partials3, W.partials4, W.S);
+        }
         ADLBR_CUDA(cudaGetLastError());
         // q = p (q aliases acc64, which the restart kernel has consumed)
         ADLBR_CUDA(cudaMemcpyAsync(W.q, W.p, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -361,8 +379,10 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
         // stop when the true residual meets rtol, when refinement stopped
         // paying (x is FP32: the true residual floors near eps32 |I + dt A|),
         // or when the budget is spent
-        if (relres <= rtol || total_iters >= maxit || restart == kMaxRestarts) break;
-        if (restart > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
+        if ((!first32 && relres <= rtol) || total_iters >= maxit || restart == kMaxRestarts) break;
+        // (not after a round that ran no iteration: the first, FP32 residual
+        // can already meet rtol where the FP64 one does not)
+        if (restart > 0 && round_iters > 0 && (relres <= 10.0 * rtol || !(relres < 0.5 * prev))) break;
         prev = relres;
         const int chunk = every > 0 ? every : 8;
         // 16-byte vector passes when every vector allows them (the workspace
@@ -405,6 +425,7 @@ static adlbr_status cg_impl(adlbr_stencils *s, const float *b, float *x, double 
             if (host.conv) break;
         }
         total_iters += host.iters;
+        round_iters = host.iters;
         cg_converged = host.conv == 1;
         if (host.conv == 3) {
             if (iters_out) *iters_out = total_iters;
