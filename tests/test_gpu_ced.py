@@ -283,3 +283,49 @@ def test_build_step_reports_a_bad_tensor():
                 ab.adlbr_stencils_destroy(h)
     err = (u1 - u2).abs().max().item() / u1.abs().max().item()
     assert err <= 1e-6, err
+
+
+def test_build_step_full_size_4096():
+    """The benchmark's timed launch: the 4096^2 CED tensor, then the build
+    fused into the operator (F16 weights, FP32 u), against the build and the
+    stand-alone step: stencils bit for bit over the whole grid, u to 1e-6, and
+    u at 20,000 sampled points against the oracle's explicit step on the
+    exported stencils."""
+    from gpu_helpers import export
+    t = torch()
+    n = 4096
+    g = ab.grid((n, n))
+    img = synth.fingerprint(n, 1).astype(np.float32)
+    u1 = t.from_numpy(img.ravel().copy()).cuda()
+    u2 = u1.clone()
+    N = n * n
+    scratch = t.empty(ab.adlbr_ced_scratch_bytes(g), dtype=t.uint8, device="cuda")
+    D = t.empty(3 * N, dtype=t.float32, device="cuda")
+    ab.adlbr_ced_tensor(g, u1, D, 1.0, 4.0, 1e-4, 1e-5, scratch)
+    acc1 = t.empty(N, dtype=t.float32, device="cuda")
+    acc2 = t.empty_like(acc1)
+    h1 = h2 = None
+    try:
+        h1 = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+        ab.adlbr_step_explicit(h1, u1, acc1, ab.F32, 0.02, 1)
+        h2 = ab.adlbr_build_step_explicit(g, D, ab.F32, ab.F16, None, u2, acc2, 0.02)
+        ab.adlbr_stencils_check(h1)
+        ab.adlbr_stencils_check(h2)
+        o1, w1 = export(h1, (n, n), ab.F16)
+        o2, w2 = export(h2, (n, n), ab.F16)
+    finally:
+        for h in (h1, h2):
+            if h:
+                ab.adlbr_stencils_destroy(h)
+    assert np.array_equal(o1, o2)
+    assert np.array_equal(w1, w2)
+    a, b = u1.double().cpu().numpy(), u2.double().cpu().numpy()
+    scale = np.abs(a).max()
+    assert np.abs(a - b).max() <= 1e-6 * scale
+    # sampled points against the oracle's step: u - dt (A u) from own and
+    # incoming terms of the exported stencils
+    from test_gpu_gather import _rows
+    uu = img.astype(np.float64).reshape(n, n)
+    zs = np.random.default_rng(3).integers(0, N, 20000)
+    ref = uu.ravel()[zs] - 0.02 * _rows(o2, w2, uu, zs, n)
+    assert np.abs(b[zs] - ref).max() <= 1e-6 * scale

@@ -260,6 +260,7 @@ def test_gather_full_size_ced_4096():
     zs = rng.integers(0, n * n, 100000)
     ref = _rows(oo, ow, uu, zs, n)
     assert np.abs(g_[zs] - ref).max() <= 1e-5 * scale
+    assert np.abs(s_[zs] - ref).max() <= 1e-5 * scale
 
 
 def _rows(oo, ow, uu, zs, n):
