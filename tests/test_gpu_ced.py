@@ -329,3 +329,30 @@ def test_build_step_full_size_4096():
     zs = np.random.default_rng(3).integers(0, N, 20000)
     ref = uu.ravel()[zs] - 0.02 * _rows(o2, w2, uu, zs, n)
     assert np.abs(b[zs] - ref).max() <= 1e-6 * scale
+
+
+def test_build_step_3d_equals_build_then_step():
+    """The 3D grid takes the two-call path inside adlbr_build_step_explicit:
+    same stencils bit for bit, same u to FP32 rounding."""
+    from gpu_helpers import export
+    t = torch()
+    shape = (20, 24, 28)
+    D = dev(synth.needle_field3d(28, seed=9, kappa=15.0)[:, :20, :24, :28].reshape(6, -1), t.float32)
+    g = ab.grid(shape)
+    u1 = dev(synth.u_uniform(shape, 4).ravel(), t.float32)
+    u2 = u1.clone()
+    h1 = h2 = None
+    try:
+        h1 = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+        dt = 0.5 / ab.adlbr_stencils_max_diag(h1)
+        sc = t.empty(ab.adlbr_step_scratch_bytes(h1, ab.F32), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(h1, u1, sc, ab.F32, dt, 1)
+        h2 = ab.adlbr_build_step_explicit(g, D, ab.F32, ab.F16, None, u2, t.empty_like(sc), dt)
+        o1, w1 = export(h1, shape, ab.F16)
+        o2, w2 = export(h2, shape, ab.F16)
+    finally:
+        for h in (h1, h2):
+            if h:
+                ab.adlbr_stencils_destroy(h)
+    assert np.array_equal(o1, o2) and np.array_equal(w1, w2)
+    assert (u1 - u2).abs().max().item() <= 1e-6 * u1.abs().max().item()
