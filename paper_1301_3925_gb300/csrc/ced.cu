@@ -271,10 +271,23 @@ __device__ __forceinline__ void load_u_window(const FusedGeom &g, int nx, int ny
     const int uox = x0 - g.R - 1 - g.S, uoy = y0 - g.R - 1 - g.S;
     const bool interior = uox >= 0 && uoy >= 0 && uox + g.UW <= nx && uoy + g.UH <= ny;
     constexpr int FNT = fused_threads<S_, R_>();
+    if (interior) {
+        // no reflection: a warp per row, each lane copying every 32nd column
+        // from one row base (constant offsets, no per-element index math:
+        // 0.249 against 0.260 ms at 4096^2, sigma 1, rho 4)
+        for (int r = threadIdx.x / 32; r < g.UH; r += FNT / 32) {
+            const float *src = u + (int64_t)(uoy + r) * nx + uox;
+            float *dst = U + r * g.UP;
+#pragma unroll 4
+            for (int c = threadIdx.x % 32; c < g.UW; c += 32) cp_async4(dst + c, src + c);
+        }
+        cp_async_commit();
+        return;
+    }
     for (int i = threadIdx.x; i < g.UH * g.UW; i += FNT) {
         const int r = i / g.UW, c = i - r * g.UW;
-        const int gy = interior ? uoy + r : reflect(uoy + r, ny);
-        const int gx = interior ? uox + c : reflect(uox + c, nx);
+        const int gy = reflect(uoy + r, ny);
+        const int gx = reflect(uox + c, nx);
         cp_async4(U + r * g.UP + c, u + (int64_t)gy * nx + gx);
     }
     cp_async_commit();
@@ -361,6 +374,29 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
     }
     __syncthreads();
     // 4. P = outer product of the centred differences, at the reflected cell
+    if (fixed && interior && g.PW * (g.PH / 11) <= FNT && g.PH % 11 == 0) {
+        // no reflection: P cell (r, c) is u_sigma cell (r + 1, c + 1); each
+        // thread walks 11 rows of one column, keeping the two u_sigma values
+        // above the current row in registers (0.257 against 0.260 ms)
+        if (threadIdx.x < g.PW * (g.PH / 11)) {
+            const int c = threadIdx.x % g.PW, r0 = (threadIdx.x / g.PW) * 11;
+            const float *s = US + r0 * g.SP + c + 1;
+            float up = s[0], mid = s[g.SP];
+#pragma unroll
+            for (int j = 0; j < 11; ++j) {
+                const float *m = s + (j + 1) * g.SP;
+                const float down = m[g.SP];
+                const float gx = __fmul_rn(0.5f, __fsub_rn(m[1], m[-1]));
+                const float gy = __fmul_rn(0.5f, __fsub_rn(down, up));
+                const int r = r0 + j;
+                P[r * g.PP + c] = __fmul_rn(gx, gx);
+                P[(g.PH + r) * g.PP + c] = __fmul_rn(gx, gy);
+                P[(2 * g.PH + r) * g.PP + c] = __fmul_rn(gy, gy);
+                up = mid;
+                mid = down;
+            }
+        }
+    } else {
     for (int i = threadIdx.x; i < g.PH * g.PW; i += FNT) {
         const int r = i / g.PW, c = i - r * g.PW;
         const int ly = (interior ? poy + r : reflect(poy + r, ny)) - soy;
@@ -371,6 +407,7 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         P[r * g.PP + c] = __fmul_rn(gx, gx);
         P[(g.PH + r) * g.PP + c] = __fmul_rn(gx, gy);
         P[(2 * g.PH + r) * g.PP + c] = __fmul_rn(gy, gy);
+    }
     }
     __syncthreads();
     // 5. Px = x pass of P over the FT output columns (lanes along rows)

@@ -514,7 +514,7 @@ adlbr_status unet_backward(adlbr_unet *n, const float *params, const float *gy, 
     // output layer: g0 = d/d d1b
     {
         const int64_t HW = (int64_t)H * W;
-        int blocks = (int)std::min<int64_t>(nb((int64_t)B * HW), 1216);
+        int blocks = (int)std::min<int64_t>(nb((int64_t)B * HW), vec_blocks());
         conv1x1_out_bwd_kernel<<<blocks, 256, 0, st>>>(B, n->c1, (int)HW, n->d1b, params + L[10].w_off, gy,
                                                       gparams + L[10].w_off, gparams + L[10].b_off, g0);
     }
