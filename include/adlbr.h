@@ -264,11 +264,14 @@ adlbr_status adlbr_step_explicit(const adlbr_stencils *s, void *u, void *scratch
  * For a 2D grid with FP32 D, F16 weights, a non-periodic boundary, nx % 4 ==
  * 0 and u 16-byte aligned (and the handle not set to the gather form) the
  * construction runs inside the operator's kernel: each point's stencil is
- * built, stored in the handle and applied by the same thread.  Otherwise
- * this is adlbr_build_stencils followed by adlbr_step_explicit.  Either way
- * the stored stencils are bit for bit those of adlbr_build_stencils, and u
- * equals the two-call result to FP32 rounding (the order of the atomic
- * additions).  Errors as the two calls; a failed build is reported, as
+ * built, stored in the handle and applied by the same thread; once the
+ * handle holds a build, each point starts from its previous stencil, which
+ * is certified exactly (and repaired, or rebuilt from scratch, where it no
+ * longer fits D).  Otherwise this is adlbr_build_stencils followed by
+ * adlbr_step_explicit.  Either way the stencils are those of
+ * adlbr_build_stencils, bit for bit as adlbr_stencils_export writes them
+ * (its canonical order and signs), and u equals the two-call result to FP32
+ * rounding (the order of the atomic additions).  Errors as the two calls; a failed build is reported, as
  * there, by adlbr_stencils_check.  If that check returns ADLBR_E_TIMEOUT (a
  * tile's window copy never arrived), the tiles concerned were neither built
  * nor stepped: the stencils and u are then undefined.

@@ -29,6 +29,7 @@ adlbr_status launch_build2d(adlbr_stencils *s, const void *D, adlbr_dtype D_t, c
         build2d_kernel<double><<<blocks, threads, 0, st>>>(s->N, (const double *)D,
                                                            (short4 *)s->offs, s->w, s->w_t, s->err);
     ADLBR_CUDA(cudaGetLastError());
+    s->built = 1;
     return ADLBR_OK;
 }
 

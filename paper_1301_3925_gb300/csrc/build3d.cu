@@ -29,7 +29,6 @@ struct V3 {
 };
 
 __device__ __forceinline__ V3 add(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 sub(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 neg(V3 a) { return V3{-a.x, -a.y, -a.z}; }
 // a - k b (exact: integers below 2^24)
 __device__ __forceinline__ V3 sub_mul(V3 a, float k, V3 b) {

@@ -116,6 +116,9 @@ struct adlbr_stencils {
     // operator form (adlbr_operator_form) and the gather table
     int op_form;
     int applies_since_build;
+    // a 2D AD-LBR build has stored stencils in offs: the fused build-and-step
+    // kernel starts each point from its previous stencil (certified)
+    int built;
     adlbr::PullTable *pull;
 };
 

@@ -90,6 +90,7 @@ struct BuildStencil {
     int64_t N;
     short4 *offs;      // the handle's stencil storage
     void *w;
+    bool warm;         // offs holds a previous build's stencils (a start for each point)
 };
 
 // acc += scale A u over the tile at (x0, y0); every thread of the block
@@ -191,7 +192,7 @@ __device__ __forceinline__ void tile2d(int nx, int ny, int bc, float scale, cons
             // (loading the next pass's tensor one pass ahead measured no faster)
             static_assert(F16W, "the fused build stores F16 weights");
             const Built2 bt = build_point2d<float>(src.D[z], src.D[src.N + z], src.D[2 * src.N + z], z, src.offs,
-                                                   src.w, ADLBR_F16, err);
+                                                   src.w, ADLBR_F16, err, src.warm);
             o = bt.o;
             weights_f16_rec(bt.rec, scale, w);
         } else if (F16W) {

@@ -96,6 +96,8 @@ __device__ __forceinline__ float gramf(float sxx, float sxy, float syy, float ux
 
 constexpr int kMaxReduce = 64;
 constexpr int kMaxFix = 256;
+// repair budget of a warm start (below): past it, the point is built cold
+constexpr int kWarmFix = 2;
 // |coordinates| <= 2047 keeps every integer of the predicates below 2^24
 constexpr int kMaxCoord = 2047;
 
@@ -109,9 +111,18 @@ struct Built2 {
 };
 
 // Builds and stores the stencil of point i from D = [[a, b], [b, c]].
+//
+// warm: offs[i] holds this point's stencil from an earlier build of the
+// same handle (the previous step of a CED loop, where D moves little).  Its
+// superbase (e, f, -e-f), if it is one (|det(e, f)| = 1, coordinates in
+// range), is certified and repaired like the reduced basis below, with a
+// budget of kWarmFix repairs; the reduction runs only where that fails.  A
+// certified S-obtuse superbase gives the unique stencil of Lemma indepBasis,
+// so the result is the cold build's (the three vectors may come in another
+// order or sign, which the canonical export removes).
 template <typename T>
 __device__ __forceinline__ Built2 build_point2d(T a, T b, T c, int64_t i, short4 *__restrict__ offs,
-                                                void *wbase, adlbr_dtype wt, int *err) {
+                                                void *wbase, adlbr_dtype wt, int *err, bool warm = false) {
     using namespace s2d;
     using WV = typename WVal<T>::type;
     WV wz[3] = {};
@@ -128,61 +139,79 @@ __device__ __forceinline__ Built2 build_point2d(T a, T b, T c, int64_t i, short4
         return Built2{make_short4(0, 0, 0, 0), make_uint2(r.x, r.y)};
     }
 
-    // (i) approximate Lagrange reduction in FP32 on S / max(a, c): the basis
-    // vectors are kept as integer-valued floats, |f|_S^2 is carried over to
-    // the next |e|_S^2, and the quotient is approximate (the result is
-    // certified exactly below, so these shortcuts can only cost repair steps)
-    float sxx, sxy, syy;
-    scaled_adj(a, b, c, sxx, sxy, syy);
-    // The Gram values of the running basis are updated, not recomputed:
-    // f' = e - q f gives |f'|^2 = |e|^2 - q (2 <e,f> - q |f|^2) and
-    // <f, f'> = <e,f> - q |f|^2.
-    float ex = 1.f, ey = 0.f, fx = 0.f, fy = 1.f;
-    float gee = sxx, gef = sxy, gff = syy;   // Gram values of e = (1, 0), f = (0, 1)
-    for (int it = 0; it < kMaxReduce; ++it) {
-        if (!(gff > 0.f)) break;
-        const float q = fminf(fmaxf(rintf(__fdividef(gef, gff)), -2048.f), 2048.f);
-        const float nx = fmaf(-q, fx, ex), ny = fmaf(-q, fy, ey);   // exact: integers below 2^24
-        if (fabsf(nx) > (float)kMaxCoord || fabsf(ny) > (float)kMaxCoord) {
-            ex = fx, ey = fy, fx = nx, fy = ny;
-            break;
-        }
-        const float gnn = fmaf(-q, fmaf(-q, gff, 2.f * gef), gee);
-        const float gfn = fmaf(-q, gff, gef);
-        const bool shorter = gff > gnn;
-        ex = fx, ey = fy, fx = nx, fy = ny;
-        gee = gff, gef = gfn, gff = gnn;
-        if (!shorter) break;
-    }
-    // (ii) orientation of f
-    if (gef > 0.f) fx = -fx, fy = -fy;
-    V2 e{ex, ey}, f{fx, fy};
-
-    // (iii) superbase, certified and repaired with exact signs
-    V2 v[3] = {e, f, V2{-e.x - f.x, -e.y - f.y}};
+    V2 v[3];
     int sg[3];
     WV val[3];
-    bool ok = false;
-    for (int fix = 0; fix < kMaxFix; ++fix) {
-        int bad = -1;
+    // (iii) below: certify the superbase v with exact signs and repair it by
+    // Selling steps, at most `budget` of them
+    auto certify = [&](int budget) {
+        for (int fix = 0;; ++fix) {
+            int bad = -1;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            T x[3];
-            float n[3];
-            terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
-            sg[k] = sign_value_nf<3>(x, n, val[k]);
-            if (sg[k] > 0 && bad < 0) bad = k;
+            for (int k = 0; k < 3; ++k) {
+                T x[3];
+                float n[3];
+                terms2(a, b, c, v[(k + 1) % 3], v[(k + 2) % 3], x, n);
+                sg[k] = sign_value_nf<3>(x, n, val[k]);
+                if (sg[k] > 0 && bad < 0) bad = k;
+            }
+            if (bad < 0) return true;
+            if (fix == budget) return false;
+            // pair (j, l) = (bad+1, bad+2) is acute: (v_j, v_l, v_bad) -> (-v_j, v_l, v_j - v_l)
+            const int j = (bad + 1) % 3, l = (bad + 2) % 3;
+            V2 vj = v[j], vl = v[l];
+            v[j] = V2{-vj.x, -vj.y};
+            v[bad] = V2{vj.x - vl.x, vj.y - vl.y};
+            if (fabsf(v[bad].x) > (float)kMaxCoord || fabsf(v[bad].y) > (float)kMaxCoord) return false;
         }
-        if (bad < 0) {
-            ok = true;
-            break;
+    };
+    bool ok = false;
+    if (warm) {
+        const short4 p = offs[i];
+        const int det = (int)p.x * p.w - (int)p.y * p.z;
+        const int tx = -(int)p.x - p.z, ty = -(int)p.y - p.w;
+        if ((det == 1 || det == -1) && abs(tx) <= kMaxCoord && abs(ty) <= kMaxCoord) {
+            v[0] = V2{(float)p.x, (float)p.y};
+            v[1] = V2{(float)p.z, (float)p.w};
+            v[2] = V2{(float)tx, (float)ty};
+            ok = certify(kWarmFix);
         }
-        // pair (j, l) = (bad+1, bad+2) is acute: (v_j, v_l, v_bad) -> (-v_j, v_l, v_j - v_l)
-        const int j = (bad + 1) % 3, l = (bad + 2) % 3;
-        V2 vj = v[j], vl = v[l];
-        v[j] = V2{-vj.x, -vj.y};
-        v[bad] = V2{vj.x - vl.x, vj.y - vl.y};
-        if (fabsf(v[bad].x) > (float)kMaxCoord || fabsf(v[bad].y) > (float)kMaxCoord) break;
+    }
+    if (!ok) {
+        // (i) approximate Lagrange reduction in FP32 on S / max(a, c): the basis
+        // vectors are kept as integer-valued floats, |f|_S^2 is carried over to
+        // the next |e|_S^2, and the quotient is approximate (the result is
+        // certified exactly below, so these shortcuts can only cost repair steps)
+        float sxx, sxy, syy;
+        scaled_adj(a, b, c, sxx, sxy, syy);
+        // The Gram values of the running basis are updated, not recomputed:
+        // f' = e - q f gives |f'|^2 = |e|^2 - q (2 <e,f> - q |f|^2) and
+        // <f, f'> = <e,f> - q |f|^2.
+        float ex = 1.f, ey = 0.f, fx = 0.f, fy = 1.f;
+        float gee = sxx, gef = sxy, gff = syy;   // Gram values of e = (1, 0), f = (0, 1)
+        for (int it = 0; it < kMaxReduce; ++it) {
+            if (!(gff > 0.f)) break;
+            const float q = fminf(fmaxf(rintf(__fdividef(gef, gff)), -2048.f), 2048.f);
+            const float nx = fmaf(-q, fx, ex), ny = fmaf(-q, fy, ey);   // exact: integers below 2^24
+            if (fabsf(nx) > (float)kMaxCoord || fabsf(ny) > (float)kMaxCoord) {
+                ex = fx, ey = fy, fx = nx, fy = ny;
+                break;
+            }
+            const float gnn = fmaf(-q, fmaf(-q, gff, 2.f * gef), gee);
+            const float gfn = fmaf(-q, gff, gef);
+            const bool shorter = gff > gnn;
+            ex = fx, ey = fy, fx = nx, fy = ny;
+            gee = gff, gef = gfn, gff = gnn;
+            if (!shorter) break;
+        }
+        // (ii) orientation of f
+        if (gef > 0.f) fx = -fx, fy = -fy;
+
+        // (iii) superbase, certified and repaired with exact signs
+        v[0] = V2{ex, ey};
+        v[1] = V2{fx, fy};
+        v[2] = V2{-ex - fx, -ey - fy};
+        ok = certify(kMaxFix - 1);
     }
     bool range = false;
 #pragma unroll

@@ -254,6 +254,78 @@ def test_build_step_equals_build_then_step(case):
     assert err <= 1e-6, err
 
 
+WARM_CASES = {
+    # the tensor the handle's stencils were built from, then the next one
+    "same_tensor": (13, "same"),
+    "after_ced_steps": (13, "steps"),
+    "unrelated_image": (13, "other"),
+    "bad_points_before": (13, "bad_first"),
+}
+
+
+@pytest.mark.parametrize("case", list(WARM_CASES))
+def test_build_step_warm_start_equals_cold_build(case):
+    """A handle that already holds stencils: the fused build-and-step kernel
+    starts each point from its previous stencil (certified and repaired, or
+    built from scratch where that fails).  The stencils must be those of a
+    fresh build of the new tensor, offsets and F16 weights bit for bit after
+    the canonical export, and u that of build-then-step, whether the new
+    tensor is the same, a few CED steps later, from an unrelated image, or
+    follows a build whose points were partly invalid (zero stencils)."""
+    from gpu_helpers import export
+    t = torch()
+    shape = (96, 160)
+    seed, kind = WARM_CASES[case]
+    g = ab.grid(shape)
+    D1n, img = _ced_D(shape, seed)
+    if kind == "same":
+        D2n = D1n
+    elif kind == "other":
+        D2n, _ = _ced_D(shape, seed + 1)
+    else:
+        D2n = D1n
+    D1 = dev(D1n, t.float32)
+    if kind == "bad_first":
+        D1 = D1.clone().reshape(3, -1)
+        D1[:, ::7] = float("nan")   # these points get the zero stencil and an error bit
+        D1 = D1.reshape(-1)
+    u = dev(img.ravel(), t.float32)
+    sc = t.empty(ab.adlbr_ced_scratch_bytes(g), dtype=t.uint8, device="cuda")
+    if kind == "steps":
+        # the tensor three CED steps later, from the GPU's own loop
+        u3 = u.clone()
+        h3 = ab.adlbr_ced_step(None, g, u3, sc, 1.0, 4.0, 1e-4, 1e-5, 0.5, 3, ab.F16)
+        ab.adlbr_stencils_destroy(h3)
+        D2 = t.empty(3 * u.numel(), dtype=t.float32, device="cuda")
+        ab.adlbr_ced_tensor(g, u3, D2, 1.0, 4.0, 1e-4, 1e-5, sc)
+    else:
+        D2 = dev(D2n, t.float32)
+    h = hc = None
+    try:
+        h = ab.adlbr_build_step_explicit(g, D1, ab.F32, ab.F16, None, u.clone(), sc, 0.02)
+        if kind == "bad_first":
+            with pytest.raises(ab.AdlbrError):
+                ab.adlbr_stencils_check(h)
+        u_w = u.clone()
+        h = ab.adlbr_build_step_explicit(g, D2, ab.F32, ab.F16, h, u_w, sc, 0.02)
+        ab.adlbr_stencils_check(h)
+        hc = ab.adlbr_build_stencils(g, D2, ab.F32, ab.F16)
+        u_c = u.clone()
+        sc2 = t.empty(ab.adlbr_step_scratch_bytes(hc, ab.F32), dtype=t.uint8, device="cuda")
+        ab.adlbr_step_explicit(hc, u_c, sc2, ab.F32, 0.02, 1)
+        ab.adlbr_stencils_check(hc)
+        o_w, w_w = export(h, shape, ab.F16)
+        o_c, w_c = export(hc, shape, ab.F16)
+    finally:
+        for hh in (h, hc):
+            if hh:
+                ab.adlbr_stencils_destroy(hh)
+    assert np.array_equal(o_w, o_c)
+    assert np.array_equal(w_w, w_c)
+    err = (u_w - u_c).abs().max().item() / u_c.abs().max().item()
+    assert err <= 1e-6, err
+
+
 def test_build_step_reports_a_bad_tensor():
     """A tensor that is not positive definite at one point: the fused kernel
     reports it as the build does (ADLBR_E_NOT_SPD from adlbr_stencils_check),
@@ -329,6 +401,44 @@ def test_build_step_full_size_4096():
     zs = np.random.default_rng(3).integers(0, N, 20000)
     ref = uu.ravel()[zs] - 0.02 * _rows(o2, w2, uu, zs, n)
     assert np.abs(b[zs] - ref).max() <= 1e-6 * scale
+
+
+def test_build_step_warm_start_full_size_4096():
+    """The benchmark's loop: four CED steps at 4096^2 through the tensor
+    stage and the fused build-and-step (every step after the first starts
+    from the previous stencils).  The handle's stencils after the last step
+    must equal a fresh build of the last tensor over the whole grid, and u
+    the build-then-step of the same tensor."""
+    from gpu_helpers import export
+    t = torch()
+    n = 4096
+    g = ab.grid((n, n))
+    N = n * n
+    u = t.from_numpy(synth.fingerprint(n, 1).astype(np.float32).ravel().copy()).cuda()
+    scratch = t.empty(ab.adlbr_ced_scratch_bytes(g), dtype=t.uint8, device="cuda")
+    D = t.empty(3 * N, dtype=t.float32, device="cuda")
+    acc = t.empty(N, dtype=t.float32, device="cuda")
+    h = hc = None
+    try:
+        for step in range(4):
+            ab.adlbr_ced_tensor(g, u, D, 1.0, 4.0, 1e-4, 1e-5, scratch)
+            if step == 3:
+                u_c = u.clone()
+            h = ab.adlbr_build_step_explicit(g, D, ab.F32, ab.F16, h, u, acc, 0.02)
+        ab.adlbr_stencils_check(h)
+        hc = ab.adlbr_build_stencils(g, D, ab.F32, ab.F16)
+        ab.adlbr_step_explicit(hc, u_c, acc, ab.F32, 0.02, 1)
+        ab.adlbr_stencils_check(hc)
+        o_w, w_w = export(h, (n, n), ab.F16)
+        o_c, w_c = export(hc, (n, n), ab.F16)
+    finally:
+        for hh in (h, hc):
+            if hh:
+                ab.adlbr_stencils_destroy(hh)
+    assert np.array_equal(o_w, o_c)
+    assert np.array_equal(w_w, w_c)
+    a, b = u.double().cpu().numpy(), u_c.double().cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()
 
 
 def test_build_step_3d_equals_build_then_step():
