@@ -264,10 +264,14 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Asynchronous copy of the (reflected) u window of the tile at (x0, y0).
+// Asynchronous copy of the (reflected) u window of the tile at (x0, y0), in
+// kParts parts issued between the passes of the previous tile (part = -1:
+// all at once).  Interior windows are split by rows; a window that needs
+// reflection is copied whole by part 0.  The last part commits the group.
+constexpr int kParts = 4;
 template <int S_, int R_>
 __device__ __forceinline__ void load_u_window(const FusedGeom &g, int nx, int ny, int x0, int y0,
-                                              const float *__restrict__ u, float *U) {
+                                              const float *__restrict__ u, float *U, int part = -1) {
     const int uox = x0 - g.R - 1 - g.S, uoy = y0 - g.R - 1 - g.S;
     const bool interior = uox >= 0 && uoy >= 0 && uox + g.UW <= nx && uoy + g.UH <= ny;
     constexpr int FNT = fused_threads<S_, R_>();
@@ -275,15 +279,17 @@ __device__ __forceinline__ void load_u_window(const FusedGeom &g, int nx, int ny
         // no reflection: a warp per row, each lane copying every 32nd column
         // from one row base (constant offsets, no per-element index math:
         // 0.249 against 0.260 ms at 4096^2, sigma 1, rho 4)
-        for (int r = threadIdx.x / 32; r < g.UH; r += FNT / 32) {
+        const int r0 = part < 0 ? 0 : part * g.UH / kParts, r1 = part < 0 ? g.UH : (part + 1) * g.UH / kParts;
+        for (int r = r0 + threadIdx.x / 32; r < r1; r += FNT / 32) {
             const float *src = u + (int64_t)(uoy + r) * nx + uox;
             float *dst = U + r * g.UP;
 #pragma unroll 4
             for (int c = threadIdx.x % 32; c < g.UW; c += 32) cp_async4(dst + c, src + c);
         }
-        cp_async_commit();
+        if (part < 0 || part == kParts - 1) cp_async_commit();
         return;
     }
+    if (part > 0) return;
     for (int i = threadIdx.x; i < g.UH * g.UW; i += FNT) {
         const int r = i / g.UW, c = i - r * g.UW;
         const int gy = reflect(uoy + r, ny);
@@ -334,11 +340,15 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
     const bool interior = uox >= 0 && uoy >= 0 && uox + g.UW <= nx && uoy + g.UH <= ny;
     cp_async_wait_all();
     __syncthreads();   // u of this tile is in place; the previous tile is done
-    if (tile + (int)gridDim.x < tiles) {
-        int nx0, ny0;
-        origin(tile + gridDim.x, nx0, ny0);
-        load_u_window<S_, R_>(g, nx, ny, nx0, ny0, u, (it & 1) ? sm : sm + g.offU1);
-    }
+    // the next tile's window, copied in parts between the passes below
+    const bool has_next = tile + (int)gridDim.x < tiles;
+    int nx0 = 0, ny0 = 0;
+    if (has_next) origin(tile + gridDim.x, nx0, ny0);
+    float *Un = (it & 1) ? sm : sm + g.offU1;
+    auto next_part = [&](int k) {
+        if (has_next) load_u_window<S_, R_>(g, nx, ny, nx0, ny0, u, Un, k);
+    };
+    next_part(0);
     constexpr int RBS = fixed ? RBS_FIXED : RBF;
     // 2. bx = x pass of u (lanes along rows, RBS outputs per thread)
     {
@@ -356,6 +366,7 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         }
     }
     __syncthreads();
+    next_part(1);
     // 3. u_sigma = y pass of bx (lanes along columns, RBS rows per thread)
     {
         const int groups = (g.SH + RBS - 1) / RBS;
@@ -373,6 +384,7 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
         }
     }
     __syncthreads();
+    next_part(2);
     // 4. P = outer product of the centred differences, at the reflected cell
     if (fixed && interior && g.PW * (g.PH / 11) <= FNT && g.PH % 11 == 0) {
         // no reflection: P cell (r, c) is u_sigma cell (r + 1, c + 1); each
@@ -411,6 +423,7 @@ __global__ void __launch_bounds__(fused_threads<S_, R_>(), 1) ced_fused_kernel(i
     }
     }
     __syncthreads();
+    next_part(3);
     // 5. Px = x pass of P over the FT output columns (lanes along rows)
     {
         constexpr int groups = FT / RBF;
