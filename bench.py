@@ -60,12 +60,12 @@ def fp32_peak_tops():
 # DRAM bytes (read + write) of one launch at 4096^2, from an ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum, one launch each,
 # second warm-up step of this benchmark's CED step)
-TRAFFIC_4096 = {"ced_fused_kernel": 67.196e6 + 140.737e6, "build2d_kernel": 201.441e6 + 222.316e6,
+TRAFFIC_4096 = {"ced_fused_kernel": 67.203e6 + 140.874e6, "build2d_kernel": 201.391e6 + 225.406e6,
                 # operator + finalize
                 "explicit_step": 402.739e6 + 48.194e6 + 134.228e6 + 19.020e6,
                 # fused build and operator + finalize (the memset's 67 MB write is
                 # not a kernel and is not counted)
-                "build_step": 471.377e6 + 294.355e6 + 134.228e6 + 19.020e6}
+                "build_step": 471.220e6 + 294.850e6 + 134.228e6 + 19.020e6}
 
 
 def parse():
