@@ -556,6 +556,32 @@ adlbr_status adlbr_batch_config(const adlbr_batch *b, int *shape_out, double *tu
 
 adlbr_status adlbr_batch_destroy(adlbr_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Block vectors of the periodic spectral study (Sec. 4, Fig. Eigen: the
+ * smallest eigenvalues of the operator on a periodic grid).  The block
+ * eigensolver needs, besides A X (adlbr_apply), the Gram matrices of its
+ * search blocks, linear combinations of their rows and the residual rows.
+ * A block is m <= 64 rows of n FP64 values on the device, row-major with row
+ * stride n.  Every sum is taken by one CTA in a fixed order: the results are
+ * deterministic.  Asynchronous on `stream`; ADLBR_E_ARG for a null pointer,
+ * m or k outside [1, 64] or n < 1.
+ * ------------------------------------------------------------------------ */
+
+/* G = A B^T: G[i * mb + j] = sum_p A[i][p] B[j][p] (device, ma * mb). */
+adlbr_status adlbr_block_dot(const double *A, int ma, const double *B, int mb, int64_t n, double *G,
+                             cudaStream_t stream);
+
+/* out = C^T S: out[r][p] = sum_i C[i * k + r] S[i][p] for r < k, i < m (the
+ * sum in order of i).  C: device, m * k, row-major.  out (k rows) must not
+ * overlap S. */
+adlbr_status adlbr_block_combine(const double *C, int m, int k, const double *S, int64_t n, double *out,
+                                 cudaStream_t stream);
+
+/* R[i] = AX[i] - theta[i] X[i] and rnorm[i] = ||R[i]||_2 for the m rows
+ * (theta, rnorm: device, m values).  R may be AX itself. */
+adlbr_status adlbr_block_residual(const double *AX, const double *X, const double *theta, int m, int64_t n,
+                                  double *R, double *rnorm, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

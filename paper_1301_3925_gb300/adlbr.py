@@ -102,6 +102,9 @@ def lib():
             "adlbr_nn_precondition": (_i32, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
             "adlbr_mse_grad": (_i32, [_vp, _vp, ctypes.c_int64, _vp,
                                       ctypes.POINTER(ctypes.c_double), _vp]),
+            "adlbr_block_dot": (_i32, [_vp, _i32, _vp, _i32, ctypes.c_int64, _vp, _vp]),
+            "adlbr_block_combine": (_i32, [_vp, _i32, _i32, _vp, ctypes.c_int64, _vp, _vp]),
+            "adlbr_block_residual": (_i32, [_vp, _vp, _vp, _i32, ctypes.c_int64, _vp, _vp, _vp]),
             "adlbr_ced_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid)]),
             "adlbr_ced_tensor": (_i32, [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp]),
@@ -292,6 +295,27 @@ def adlbr_mse_grad(y, t, n, gy, want_loss=True, stream=None):
     _check(lib().adlbr_mse_grad(_ptr(y), _ptr(t), int(n), _ptr(gy),
                                 ctypes.byref(v) if want_loss else None, _stream(stream)))
     return v.value if want_loss else None
+
+
+def adlbr_block_dot(A, B, G, stream=None):
+    """G = A B^T for device FP64 blocks A (ma x n), B (mb x n), G (ma x mb)."""
+    ma, n = A.shape
+    mb = B.shape[0]
+    _check(lib().adlbr_block_dot(_ptr(A), int(ma), _ptr(B), int(mb), int(n), _ptr(G), _stream(stream)))
+
+
+def adlbr_block_combine(C, S, out, stream=None):
+    """out = C^T S for device FP64 C (m x k), S (m x n), out (k x n)."""
+    m, k = C.shape
+    _check(lib().adlbr_block_combine(_ptr(C), int(m), int(k), _ptr(S), int(S.shape[1]), _ptr(out),
+                                     _stream(stream)))
+
+
+def adlbr_block_residual(AX, X, theta, R, rnorm, stream=None):
+    """R = AX - theta X row by row and rnorm = the rows' 2-norms (device FP64)."""
+    m, n = X.shape
+    _check(lib().adlbr_block_residual(_ptr(AX), _ptr(X), _ptr(theta), int(m), int(n), _ptr(R), _ptr(rnorm),
+                                      _stream(stream)))
 
 
 def adlbr_ced_scratch_bytes(g):

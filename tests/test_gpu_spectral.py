@@ -74,3 +74,53 @@ def test_scheme_eigenvalues_converge_on_gpu():
             ab.adlbr_stencils_destroy(h)
         errs.append(np.abs(theta * n * n - cont)[1:].max() / cont[1:].max())
     assert errs[1] < errs[0] / 3 and errs[1] < 5e-3, errs
+
+
+@pytest.mark.parametrize("ma,mb,n", [(5, 7, 1037), (21, 21, 256), (64, 3, 5000), (1, 1, 1)])
+def test_block_kernels_match_their_definitions(ma, mb, n):
+    """The eigensolver's block kernels against their plain definitions in
+    FP64 (numpy): G = A B^T, C^T S, and R = AX - theta X with its row norms,
+    on ragged lengths and the largest block (64 rows); twice, to check that
+    the fixed-order sums give the same bits."""
+    t = torch()
+    rng = np.random.default_rng(ma * 1000 + n)
+    A = rng.standard_normal((ma, n))
+    B = rng.standard_normal((mb, n))
+    C = rng.standard_normal((ma, mb))
+    th = rng.standard_normal(ma)
+    Ad, Bd = t.from_numpy(A).cuda(), t.from_numpy(B).cuda()
+    G = t.empty((ma, mb), dtype=t.float64, device="cuda")
+    ab.adlbr_block_dot(Ad, Bd, G)
+    G1 = G.cpu().numpy()
+    ab.adlbr_block_dot(Ad, Bd, G)
+    assert np.array_equal(G.cpu().numpy(), G1)
+    ref = A @ B.T
+    assert np.abs(G1 - ref).max() <= 1e-13 * max(1.0, np.abs(A).max() * np.abs(B).max() * n)
+    out = t.empty((mb, n), dtype=t.float64, device="cuda")
+    ab.adlbr_block_combine(t.from_numpy(C).cuda(), Ad, out)
+    assert np.abs(out.cpu().numpy() - C.T @ A).max() <= 1e-13 * ma * np.abs(C).max() * np.abs(A).max()
+    AX = Bd[:1].repeat(ma, 1)
+    AXn = AX.cpu().numpy()
+    R = t.empty_like(Ad)
+    rn = t.empty(ma, dtype=t.float64, device="cuda")
+    ab.adlbr_block_residual(AX, Ad, t.from_numpy(th).cuda(), R, rn)
+    Rref = AXn - th[:, None] * A
+    scale = (np.abs(AXn) + np.abs(th[:, None] * A)).max()
+    assert np.abs(R.cpu().numpy() - Rref).max() <= 4e-16 * scale
+    assert np.allclose(rn.cpu().numpy(), np.linalg.norm(Rref, axis=1), rtol=1e-13, atol=0)
+    # in place: R = AX
+    ab.adlbr_block_residual(AX, Ad, t.from_numpy(th).cuda(), AX, rn)
+    assert np.array_equal(AX.cpu().numpy(), R.cpu().numpy())
+
+
+def test_block_kernels_refuse_bad_shapes():
+    t = torch()
+    A = t.zeros((65, 8), dtype=t.float64, device="cuda")
+    G = t.empty((65, 65), dtype=t.float64, device="cuda")
+    with pytest.raises(ab.AdlbrError) as ei:
+        ab.adlbr_block_dot(A, A, G)
+    assert ei.value.status == 1
+    C = t.zeros((65, 2), dtype=t.float64, device="cuda")
+    out = t.empty((2, 8), dtype=t.float64, device="cuda")
+    with pytest.raises(ab.AdlbrError):
+        ab.adlbr_block_combine(C, A, out)
