@@ -132,3 +132,31 @@ def tensor_from_J3(J, alpha, C):
 
 def ced_tensor3(u, sigma, rho, alpha, C):
     return np.stack(tensor_from_J3(structure_tensor3(u, sigma, rho), alpha, C))
+
+
+# Edge-enhancing diffusion in 3D (Sec. 5, the 3D MRI experiment): the same
+# J_rho and eigenvectors v1, v2, v3 (eigenvalues mu1 >= mu2 >= mu3); D's
+# eigenvalues are lambda1 = 1 - exp(-C / mu1^2) on v1, lambda2 = 1 -
+# exp(-C / mu2^2) on v2 and lambda3 = 1 on v3.  Readings: exp(-C / 0) = 0
+# (lambda = 1 where mu = 0, as in the CED definition), and 1 - exp(-x) is
+# evaluated as -expm1(-x), its value without cancellation for small x.
+
+def tensor_from_J3_eed(J, C):
+    """D(J) of edge-enhancing diffusion (numpy's symmetric eigensolver)."""
+    Jxx, Jyy, Jzz, Jxy, Jxz, Jyz = (np.asarray(a, np.float64) for a in J)
+    M = np.stack([np.stack([Jxx, Jxy, Jxz], -1), np.stack([Jxy, Jyy, Jyz], -1),
+                  np.stack([Jxz, Jyz, Jzz], -1)], -2)
+    mu, V = np.linalg.eigh(M)                      # ascending: mu[..., 2] = mu1
+
+    def lam(m):
+        q = m * m
+        pos = q > 0
+        return np.where(pos, -np.expm1(-C / np.where(pos, q, 1.0)), 1.0)
+
+    L = np.stack([np.ones_like(mu[..., 0]), lam(mu[..., 1]), lam(mu[..., 2])], -1)   # on v3, v2, v1
+    D = np.einsum("...ik,...k,...jk->...ij", V, L, V)
+    return D[..., 0, 0], D[..., 1, 1], D[..., 2, 2], D[..., 0, 1], D[..., 0, 2], D[..., 1, 2]
+
+
+def eed_tensor3(u, sigma, rho, C):
+    return np.stack(tensor_from_J3_eed(structure_tensor3(u, sigma, rho), C))

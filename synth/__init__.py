@@ -179,6 +179,29 @@ def radial3d(n, seed, R=0.5, noise_var=0.5):
     return u0, u0 + rng(seed).normal(0.0, np.sqrt(noise_var), u0.shape)
 
 
+def shells3d(shape, seed, noise=0.15, n_blobs=6):
+    """Stand-in for the paper's 256 x 256 x 100 MRI volume (Sec. 5, 3D MRI
+    data), which is not available here: nested ellipsoidal shells with
+    piecewise-constant intensities (outer layer 0.6, shell 1.0, interior
+    0.4) and n_blobs inner balls of random centre, radius and intensity,
+    on the cell-centred grid of shape (nz, ny, nx) over a unit box per axis;
+    plus N(0, noise^2) per voxel.  Returns (clean, noisy), [z, y, x]."""
+    g = rng(seed)
+    axes = [(np.arange(n) + 0.5) / n - 0.5 for n in shape]
+    Z, Y, X = np.meshgrid(*axes, indexing="ij")
+    r = np.sqrt((X / 0.42) ** 2 + (Y / 0.46) ** 2 + (Z / 0.45) ** 2)
+    u = np.zeros(shape)
+    u[r < 1.0] = 0.6
+    u[r < 0.93] = 1.0
+    u[r < 0.85] = 0.4
+    for _ in range(n_blobs):
+        c = g.uniform(-0.25, 0.25, 3)
+        rad = g.uniform(0.04, 0.1)
+        val = g.uniform(0.1, 0.9)
+        u[np.sqrt((Z - c[0]) ** 2 + (Y - c[1]) ** 2 + (X - c[2]) ** 2) < rad] = val
+    return u, u + g.normal(0.0, noise, shape)
+
+
 def batch_items(seed=100, n_images=64, n_volumes=8, img_sides=(256, 2048), vol_sides=(64, 192),
                 kappa=(5.0, 100.0)):
     """Uneven batch: per item a dict with its shape, tensor-field seed and

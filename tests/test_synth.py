@@ -106,6 +106,17 @@ def test_radial3d_recipe():
     assert abs(e.mean()) < 0.02 and abs(e.var() - var) < 0.02
 
 
+def test_shells3d_recipe():
+    u0, noisy = synth.shells3d((20, 32, 28), 5)
+    assert u0.shape == (20, 32, 28)
+    # the layers' intensities, the outside, and the blobs' values in (0.1, 0.9)
+    vals = set(np.unique(u0).round(12))
+    assert {0.0, 0.6, 1.0} <= vals and all(0.0 <= v <= 1.0 for v in vals)
+    assert abs(np.std(noisy - u0) - 0.15) < 0.01
+    a, b = synth.shells3d((20, 32, 28), 5)
+    assert np.array_equal(a, u0) and np.array_equal(b, noisy)
+
+
 def test_batch_items_recipe():
     items = synth.batch_items()
     img = [it for it in items if it["dim"] == 2]
