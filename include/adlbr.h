@@ -496,6 +496,22 @@ adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, dou
                               cudaStream_t stream);
 
 /*
+ * adlbr_eed_tensor -- the edge-enhancing diffusion tensor of the 3D MRI
+ * experiment (Sec. 5): J_rho and its eigenvectors v1, v2, v3 (eigenvalues
+ * mu1 >= mu2 >= mu3) as in adlbr_ced_tensor, and D with the eigenvalues
+ * lambda1 = 1 - exp(-C / mu1^2) on v1, lambda2 = 1 - exp(-C / mu2^2) on v2,
+ * lambda3 = 1 on v3 (exp(-C/0) = 0).  The eigenvalues lie in (0, 1], so
+ * kappa(D) = (lambda_max / lambda_min)^(1/2) grows as C falls.
+ *
+ *  g        3D grid (ADLBR_E_SHAPE otherwise).
+ *  u, D, scratch  as adlbr_ced_tensor (D: planes Dxx, Dyy, Dzz, Dxy, Dxz, Dyz).
+ *  sigma, rho  standard deviations as adlbr_ced_tensor; C > 0 and finite
+ *           (ADLBR_E_ARG otherwise).
+ */
+adlbr_status adlbr_eed_tensor(const adlbr_grid *g, const float *u, float *D, double sigma, double rho, double C,
+                              void *scratch, cudaStream_t stream);
+
+/*
  * adlbr_ced_stencils -- adlbr_ced_tensor followed by adlbr_build_stencils
  * (F32 tensor, weights stored as w_t): the AD-LBR stencils of
  * D(J_rho(grad u_sigma)), the re-stencil of one CED step.  D goes through

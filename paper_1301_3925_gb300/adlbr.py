@@ -108,6 +108,8 @@ def lib():
             "adlbr_ced_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Grid)]),
             "adlbr_ced_tensor": (_i32, [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+            "adlbr_eed_tensor": (_i32, [ctypes.POINTER(Grid), _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _vp, _vp]),
             "adlbr_ced_stencils": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(Grid), _vp, _vp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _i32, _vp]),
@@ -325,6 +327,11 @@ def adlbr_ced_scratch_bytes(g):
 def adlbr_ced_tensor(g, u, D, sigma, rho, alpha, C, scratch, stream=None):
     _check(lib().adlbr_ced_tensor(ctypes.byref(g), _ptr(u), _ptr(D), float(sigma), float(rho),
                                   float(alpha), float(C), _ptr(scratch), _stream(stream)))
+
+
+def adlbr_eed_tensor(g, u, D, sigma, rho, C, scratch, stream=None):
+    _check(lib().adlbr_eed_tensor(ctypes.byref(g), _ptr(u), _ptr(D), float(sigma), float(rho), float(C),
+                                  _ptr(scratch), _stream(stream)))
 
 
 def adlbr_ced_step(h, g, u, scratch, sigma, rho, alpha, C, dt, nsteps, w_t, stream=None):

@@ -383,6 +383,14 @@ adlbr_status adlbr_ced_tensor(const adlbr_grid *g, const float *u, float *D, dou
     return launch_ced_tensor((int)g->n[0], (int)g->n[1], u, D, sigma, rho, alpha, C, scratch, stream);
 }
 
+adlbr_status adlbr_eed_tensor(const adlbr_grid *g, const float *u, float *D, double sigma, double rho, double C,
+                              void *scratch, cudaStream_t stream) {
+    ADLBR_NVTX("adlbr_eed_tensor");
+    if (!valid_grid(g) || g->dim != 3) return fail(ADLBR_E_SHAPE, "edge-enhancing diffusion needs a valid 3D grid");
+    if (!u || !D || !scratch) return fail(ADLBR_E_ARG, "null buffer");
+    return launch_eed_tensor3d((int)g->n[0], (int)g->n[1], (int)g->n[2], u, D, sigma, rho, C, scratch, stream);
+}
+
 adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const float *u,
                                 void *scratch, double sigma, double rho, double alpha, double C,
                                 adlbr_dtype w_t, cudaStream_t stream) {

@@ -8,6 +8,11 @@
 // exp(-C/0) = 0.  Readings as in 2D: standard deviations, truncation at
 // int(3 s + 0.5), normalised taps, every stage reflects its own input.
 //
+// The edge-enhancing tensor of the 3D MRI experiment (Sec. 5) shares J_rho
+// and the eigenvectors and takes
+//   lambda1 = 1 - exp(-C / mu1^2), lambda2 = 1 - exp(-C / mu2^2), lambda3 = 1,
+// with exp(-C/0) = 0 and 1 - exp(-x) evaluated as -expm1(-x).
+//
 // Kernels: one Gaussian pass per axis (x, y, z) on C channels, one thread per
 // output (neighbours read from L1/L2; a warp covers consecutive x, so every
 // axis reads coalesced rows), the gradient outer product, and the 3 x 3
@@ -102,6 +107,13 @@ __device__ __forceinline__ float lam_of(float d, float alpha, float C) {
     return fmaf(1.f - alpha, expf(-C / (d * d)), alpha);
 }
 
+// lambda of the edge-enhancing tensor for the eigenvalue m of J
+__device__ __forceinline__ float eed_lam(float m, float C) {
+    const float q = m * m;
+    return q > 0.f ? -expm1f(-C / q) : 1.f;
+}
+
+template <bool EED>
 __global__ void __launch_bounds__(BT) tensor3_kernel(int64_t N, const float *__restrict__ J, float *__restrict__ D,
                                                      float alpha, float C) {
     const int64_t i = (int64_t)blockIdx.x * BT + threadIdx.x;
@@ -125,7 +137,16 @@ __global__ void __launch_bounds__(BT) tensor3_kernel(int64_t N, const float *__r
     if (mu[o[0]] < mu[o[1]]) { const int t = o[0]; o[0] = o[1]; o[1] = t; }
     if (mu[o[1]] < mu[o[2]]) { const int t = o[1]; o[1] = o[2]; o[2] = t; }
     if (mu[o[0]] < mu[o[1]]) { const int t = o[0]; o[0] = o[1]; o[1] = t; }
-    const float l[3] = {alpha, lam_of(mu[o[0]] - mu[o[1]], alpha, C), lam_of(mu[o[0]] - mu[o[2]], alpha, C)};
+    float l[3];
+    if (EED) {
+        l[0] = eed_lam(mu[o[0]], C);
+        l[1] = eed_lam(mu[o[1]], C);
+        l[2] = 1.f;
+    } else {
+        l[0] = alpha;
+        l[1] = lam_of(mu[o[0]] - mu[o[1]], alpha, C);
+        l[2] = lam_of(mu[o[0]] - mu[o[2]], alpha, C);
+    }
     float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     constexpr int R[6] = {0, 1, 2, 0, 0, 1}, S[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
@@ -142,11 +163,10 @@ __global__ void __launch_bounds__(BT) tensor3_kernel(int64_t N, const float *__r
 
 size_t ced_tensor3d_scratch_bytes(int64_t N) { return (size_t)N * sizeof(float) * 12; }
 
-adlbr_status launch_ced_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
-                                 double alpha, double C, void *scratch, cudaStream_t st) {
-    ADLBR_NVTX("tensor");
-    if (!(sigma > 0) || !(rho > 0) || !(alpha > 0 && alpha <= 1) || !(C >= 0))
-        return fail(ADLBR_E_ARG, "bad CED parameters");
+namespace {
+
+adlbr_status tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho, double alpha,
+                      double C, bool eed, void *scratch, cudaStream_t st) {
     const int rs = radius_of(sigma), rr = radius_of(rho);
     if (rs > kMaxR || rr > kMaxR) return fail(ADLBR_E_ARG, "Gaussian radius above %d", kMaxR);
     const Taps ts = make_taps(sigma), tr = make_taps(rho);
@@ -160,9 +180,30 @@ adlbr_status launch_ced_tensor3d(int nx, int ny, int nz, const float *u, float *
     blur3_kernel<6, 0><<<g, BT, 0, st>>>(nx, ny, nz, N, rr, tr, B, A);
     blur3_kernel<6, 1><<<g, BT, 0, st>>>(nx, ny, nz, N, rr, tr, A, B);
     blur3_kernel<6, 2><<<g, BT, 0, st>>>(nx, ny, nz, N, rr, tr, B, A);
-    tensor3_kernel<<<blocks_for(N, BT), BT, 0, st>>>(N, A, D, (float)alpha, (float)C);
+    if (eed)
+        tensor3_kernel<true><<<blocks_for(N, BT), BT, 0, st>>>(N, A, D, 0.f, (float)C);
+    else
+        tensor3_kernel<false><<<blocks_for(N, BT), BT, 0, st>>>(N, A, D, (float)alpha, (float)C);
     ADLBR_CUDA(cudaGetLastError());
     return ADLBR_OK;
+}
+
+}  // namespace
+
+adlbr_status launch_ced_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
+                                 double alpha, double C, void *scratch, cudaStream_t st) {
+    ADLBR_NVTX("tensor");
+    if (!(sigma > 0) || !(rho > 0) || !(alpha > 0 && alpha <= 1) || !(C >= 0))
+        return fail(ADLBR_E_ARG, "bad CED parameters");
+    return tensor3d(nx, ny, nz, u, D, sigma, rho, alpha, C, false, scratch, st);
+}
+
+adlbr_status launch_eed_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
+                                 double C, void *scratch, cudaStream_t st) {
+    ADLBR_NVTX("tensor");
+    // C > 0: with C = 0 every direction of non-zero mu would get lambda = 0
+    if (!(sigma > 0) || !(rho > 0) || !(C > 0) || !std::isfinite(C)) return fail(ADLBR_E_ARG, "bad EED parameters");
+    return tensor3d(nx, ny, nz, u, D, sigma, rho, 0.0, C, true, scratch, st);
 }
 
 }  // namespace adlbr

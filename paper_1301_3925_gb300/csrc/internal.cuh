@@ -297,6 +297,8 @@ size_t ced_tensor_scratch_bytes(int64_t N);
 size_t ced_tensor3d_scratch_bytes(int64_t N);
 adlbr_status launch_ced_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
                                  double alpha, double C, void *scratch, cudaStream_t st);
+adlbr_status launch_eed_tensor3d(int nx, int ny, int nz, const float *u, float *D, double sigma, double rho,
+                                 double C, void *scratch, cudaStream_t st);
 adlbr_status launch_ced_tensor(int nx, int ny, const float *u, float *D, double sigma, double rho,
                                double alpha, double C, void *scratch, cudaStream_t st);
 // CED tensor stage fused with the 2D stencil construction into handle s
