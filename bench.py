@@ -972,30 +972,65 @@ def cpu_baseline(budget_s=12.0, side=1024, all_side=512, all_budget_s=10.0):
                         "cpu_model": model, "nproc": ncpu}
 
 
+def _ref_worker(k, crop, warmup, steps, barrier, out):
+    """One process of the reference arm: `warmup` untimed CED steps of the
+    oracle on its copy of the crop, then (after every process has reached the
+    barrier) `steps` timed ones; puts (k, seconds) on `out`."""
+    oracle_ced_steps(crop[:64, :64].copy(), 1)
+    u = crop
+    for _ in range(warmup):
+        u = oracle_ced_steps(u, 1)
+    barrier.wait(timeout=900)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = oracle_ced_steps(u, 1)
+    out.put((k, time.perf_counter() - t0))
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on every host core.
+    One process per core (spawned), each advancing its own copy of the top-left
+    512^2 crop of the 4096^2 workload; a step is one CED step on every core at
+    once, timed from a common barrier to the slowest process."""
+    import multiprocessing as mp
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import synth
     side = 512
-    img = synth.fingerprint(N_SIDE, SEED)[:side, :side].copy()
-    oracle_ced_steps(img[:64, :64].copy(), 1)
-    u = img
-    for _ in range(args.warmup):
-        u = oracle_ced_steps(u, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u = oracle_ced_steps(u, 1)
-    el = time.perf_counter() - t0
-    value = args.steps * side * side / el / 1e9
-    sample = ("each step: one CED step of the FP64 oracle (numpy tensor stage, C stencils and "
-              "operator) on the top-left %dx%d crop of the 4096^2 workload, single thread" % (side, side))
+    crop = synth.fingerprint(N_SIDE, SEED)[:side, :side].copy()
+    model, ncpu = cpu_model()
+    one_thread_env()
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(ncpu), ctx.Queue()
+    procs = [ctx.Process(target=_ref_worker, args=(k, crop, args.warmup, args.steps, barrier, out))
+             for k in range(ncpu)]
+    for p in procs:
+        p.start()
+    import queue
+    spans = []
+    while len(spans) < ncpu:
+        try:
+            spans.append(out.get(timeout=5)[1])
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in procs):
+                for p in procs:
+                    if p.is_alive():
+                        p.terminate()
+                raise RuntimeError("a reference-arm process failed")
+    for p in procs:
+        p.join(timeout=60)
+    el = max(spans)
+    value = ncpu * args.steps * side * side / el / 1e9
+    sample = ("each step: one CED step of the FP64 oracle (numpy tensor stage, C stencils and operator) "
+              "on every host core at once, %d processes (spawned, one thread each), each on its own copy "
+              "of the top-left %dx%d crop of the 4096^2 workload; CPU %s" % (ncpu, side, side, model))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncpu, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
