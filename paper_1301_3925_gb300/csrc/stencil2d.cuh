@@ -128,6 +128,9 @@ __device__ __forceinline__ Built2 build_point2d(T a, T b, T c, int64_t i, short4
                                                 void *wbase, adlbr_dtype wt, int *err, bool warm = false) {
     using namespace s2d;
     using WV = typename WVal<T>::type;
+    // the previous stencil is read first, so that its load overlaps the
+    // tensor's and the tests below
+    const short4 p = warm ? offs[i] : make_short4(0, 0, 0, 0);
     WV wz[3] = {};
     int code = 0;
     if (!finite(a) || !finite(b) || !finite(c)) {
@@ -170,7 +173,6 @@ __device__ __forceinline__ Built2 build_point2d(T a, T b, T c, int64_t i, short4
     };
     bool ok = false;
     if (warm) {
-        const short4 p = offs[i];
         const int det = (int)p.x * p.w - (int)p.y * p.z;
         const int tx = -(int)p.x - p.z, ty = -(int)p.y - p.w;
         if ((det == 1 || det == -1) && abs(tx) <= kMaxCoord && abs(ty) <= kMaxCoord) {
