@@ -65,7 +65,7 @@ TRAFFIC_4096 = {"ced_fused_kernel": 67.203e6 + 140.874e6, "build2d_kernel": 201.
                 "explicit_step": 402.739e6 + 48.194e6 + 134.228e6 + 19.020e6,
                 # fused build and operator + finalize (the memset's 67 MB write is
                 # not a kernel and is not counted)
-                "build_step": 471.220e6 + 294.850e6 + 134.228e6 + 19.020e6}
+                "build_step": 471.089e6 + 294.640e6 + 134.228e6 + 19.020e6}
 
 
 def parse():
