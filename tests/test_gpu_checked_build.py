@@ -1,6 +1,7 @@
 """The bounds-checked build of the library (libadlbr_checked.so) runs the
 GPU parity suites of the stencil builds, the operator in both forms, the
-A-NN scheme, the CED pipeline and the batched step with every guard on:
+A-NN scheme, the CED pipeline (2D, and 3D with both tensors), the spectral
+study's block kernels and the batched step with every guard on:
 each of those tests compares with the oracle as in the normal build, and
 any failed index or stencil-radius check would surface as ADLBR_E_INTERNAL
 from adlbr_stencils_check or adlbr_stencils_destroy (the tests destroy every
@@ -13,7 +14,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_stencils.py", "tests/test_gpu_apply.py", "tests/test_gpu_gather.py",
-          "tests/test_gpu_ann.py", "tests/test_gpu_ced.py", "tests/test_gpu_batch.py"]
+          "tests/test_gpu_ann.py", "tests/test_gpu_ced.py", "tests/test_gpu_batch.py",
+          "tests/test_gpu_ced3d.py", "tests/test_gpu_spectral.py"]
 
 
 @pytest.mark.gpu
