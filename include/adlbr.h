@@ -525,9 +525,11 @@ adlbr_status adlbr_ced_stencils(adlbr_stencils **s, const adlbr_grid *g, const f
 /*
  * adlbr_ced_step -- nsteps steps of the CED loop of Sec. 4.4 with a frozen
  * tensor per step (D_n = D(u(n dt)), Sec. 1): tensor (adlbr_ced_tensor),
- * stencils (adlbr_build_stencils into *s, allocated on the first call and
- * rebuilt in place afterwards, weights stored as w_t), one explicit step
- * u <- u - dt A u.  u is FP32 and updated in place.
+ * then stencils and one explicit step u <- u - dt A u as
+ * adlbr_build_step_explicit (the stencils of adlbr_build_stencils into *s,
+ * allocated on the first call and rebuilt in place afterwards, weights
+ * stored as w_t; on the grids it names, built inside the operator's kernel
+ * from each point's previous stencil).  u is FP32 and updated in place.
  */
 adlbr_status adlbr_ced_step(adlbr_stencils **s, const adlbr_grid *g, float *u, void *scratch,
                             double sigma, double rho, double alpha, double C, double dt,
